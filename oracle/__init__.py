@@ -1,0 +1,244 @@
+"""Oracle for the hyperbolic self-gravity scheme (arXiv 1602.05700) -- TEST INFRASTRUCTURE ONLY.
+
+Plain FP64 CPU reference of the wave-equation replacement of Poisson's equation (Sec. 1, Eq. HNeq.), stepped as
+described in Sec. 2 and with the outer boundary conditions of Sec. 2 and Sec. 4.  The arithmetic lives in
+``hg_oracle.c`` (plain C, single thread, no fused multiply-add contraction); this module only marshals numpy
+arrays to it.  Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py`` may import
+it: the product library never does, and the two share no code.
+
+Every function here is pinned by ``tests/test_oracle_pins.py`` against something other than itself (a DST
+Poisson solve, the exact discrete plane wave, the Green's-function sum, the analytic sphere, the spherical
+harmonic addition theorem, a sparse direct solve with the Robin relation, central finite differences).
+
+Arrays: a *ghosted* array has shape (nz+2, ny+2, nx+2) with the interior at [1:-1, 1:-1, 1:-1]; an *interior*
+array has shape (nz, ny, nx).  Only face ghosts are meaningful; edge and corner ghosts stay zero.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from dataclasses import dataclass
+
+import numpy as np
+
+BC_DIRICHLET = 0
+BC_ROBIN = 1
+BC_PERIODIC = 2
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "hg_oracle.c")
+_LIB_DIR = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_LIB_DIR, "libhgoracle.so")
+
+
+def build(force: bool = False) -> str:
+    """Compile hg_oracle.c with gcc (-O2, no FMA contraction, no fast-math) into oracle/_build/."""
+    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
+        return _LIB
+    os.makedirs(_LIB_DIR, exist_ok=True)
+    tmp = _LIB + f".tmp{os.getpid()}"
+    subprocess.check_call(["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+                           "-o", tmp, _SRC, "-lm"])
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+class _OgGrid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int), ("bc", ctypes.c_int),
+                ("h", ctypes.c_double), ("x0", ctypes.c_double), ("y0", ctypes.c_double), ("z0", ctypes.c_double),
+                ("c", ctypes.c_double), ("G", ctypes.c_double), ("dt", ctypes.c_double)]
+
+
+_lib = None
+
+
+def _L():
+    global _lib
+    if _lib is None:
+        lib = ctypes.CDLL(build())
+        P = ctypes.POINTER
+        d = ctypes.c_double
+        dp = P(d)
+        gp = P(_OgGrid)
+        lib.og_mean.restype = d
+        lib.og_mean.argtypes = [gp, dp]
+        lib.og_mass.restype = d
+        lib.og_mass.argtypes = [gp, dp]
+        lib.og_real_ylm.argtypes = [ctypes.c_int, d, d, d, dp]
+        lib.og_moments.argtypes = [gp, dp, ctypes.c_int, dp]
+        lib.og_multipole_phi.restype = d
+        lib.og_multipole_phi.argtypes = [gp, ctypes.c_int, dp, d, d, d]
+        lib.og_fill_multipole_ghosts.argtypes = [gp, ctypes.c_int, dp, dp]
+        lib.og_fill_periodic_ghosts.argtypes = [gp, dp]
+        lib.og_fill_robin_static_ghosts.argtypes = [gp, dp]
+        lib.og_step.argtypes = [gp, dp, dp, dp, dp]
+        lib.og_run.argtypes = [gp, dp, dp, dp, ctypes.c_int, dp]
+        lib.og_accel.argtypes = [gp, dp, dp, dp, dp]
+        lib.og_residual.argtypes = [gp, dp, dp, dp]
+        lib.og_compare.argtypes = [gp, dp, dp, dp]
+        lib.og_adjoint.argtypes = [gp, dp, ctypes.c_int, dp]
+        _lib = lib
+    return _lib
+
+
+def _p(a: np.ndarray):
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+@dataclass
+class Grid:
+    """Grid of nx*ny*nz cubic cells of side h; cell (i,j,k) is centred at origin + ((i,j,k) + 1/2) h."""
+    nx: int
+    ny: int
+    nz: int
+    h: float
+    origin: tuple
+    c: float
+    G: float
+    dt: float
+    bc: int
+
+    def _s(self) -> _OgGrid:
+        return _OgGrid(self.nx, self.ny, self.nz, self.bc, self.h, self.origin[0], self.origin[1], self.origin[2],
+                       self.c, self.G, self.dt)
+
+    @property
+    def ghosted_shape(self):
+        return (self.nz + 2, self.ny + 2, self.nx + 2)
+
+    @property
+    def shape(self):
+        return (self.nz, self.ny, self.nx)
+
+    def centres(self, ghosts: bool = False):
+        """Cell-centre coordinate arrays (z, y, x order of axes), interior or ghosted."""
+        o = 1 if ghosts else 0
+        xs = self.origin[0] + (np.arange(-o, self.nx + o) + 0.5) * self.h
+        ys = self.origin[1] + (np.arange(-o, self.ny + o) + 0.5) * self.h
+        zs = self.origin[2] + (np.arange(-o, self.nz + o) + 0.5) * self.h
+        Z, Y, X = np.meshgrid(zs, ys, xs, indexing="ij")
+        return X, Y, Z
+
+
+def unit_cube(n: int, c: float, G: float, cfl: float, bc: int, ny: int | None = None, nz: int | None = None) -> Grid:
+    """n^3 (or n x ny x nz) cells of side 1/n, lower corner at -1/2 in every axis; dt = cfl h / (c sqrt 3)."""
+    h = 1.0 / n
+    return Grid(n, ny or n, nz or n, h, (-0.5, -0.5, -0.5), c, G, cfl * h / (c * np.sqrt(3.0)), bc)
+
+
+def ghosted(g: Grid, interior: np.ndarray | None = None) -> np.ndarray:
+    a = np.zeros(g.ghosted_shape)
+    if interior is not None:
+        a[1:-1, 1:-1, 1:-1] = interior
+    return a
+
+
+def interior(a: np.ndarray) -> np.ndarray:
+    return np.ascontiguousarray(a[1:-1, 1:-1, 1:-1])
+
+
+def mean(g: Grid, rho: np.ndarray) -> float:
+    rho = np.ascontiguousarray(rho, dtype=np.float64)
+    return _L().og_mean(ctypes.byref(g._s()), _p(rho))
+
+
+def mass(g: Grid, rho: np.ndarray) -> float:
+    rho = np.ascontiguousarray(rho, dtype=np.float64)
+    return _L().og_mass(ctypes.byref(g._s()), _p(rho))
+
+
+def real_ylm(lmax: int, x: float, y: float, z: float) -> np.ndarray:
+    Y = np.zeros((lmax + 1) ** 2)
+    _L().og_real_ylm(lmax, x, y, z, _p(Y))
+    return Y
+
+
+def moments(g: Grid, rho: np.ndarray, lmax: int) -> np.ndarray:
+    rho = np.ascontiguousarray(rho, dtype=np.float64)
+    Q = np.zeros((lmax + 1) ** 2)
+    _L().og_moments(ctypes.byref(g._s()), _p(rho), lmax, _p(Q))
+    return Q
+
+
+def multipole_phi(g: Grid, lmax: int, Q: np.ndarray, x: float, y: float, z: float) -> float:
+    Q = np.ascontiguousarray(Q, dtype=np.float64)
+    return _L().og_multipole_phi(ctypes.byref(g._s()), lmax, _p(Q), x, y, z)
+
+
+def fill_multipole_ghosts(g: Grid, lmax: int, Q: np.ndarray, phi: np.ndarray) -> None:
+    Q = np.ascontiguousarray(Q, dtype=np.float64)
+    _L().og_fill_multipole_ghosts(ctypes.byref(g._s()), lmax, _p(Q), _p(phi))
+
+
+def fill_periodic_ghosts(g: Grid, phi: np.ndarray) -> None:
+    _L().og_fill_periodic_ghosts(ctypes.byref(g._s()), _p(phi))
+
+
+def fill_robin_static_ghosts(g: Grid, phi: np.ndarray) -> None:
+    _L().og_fill_robin_static_ghosts(ctypes.byref(g._s()), _p(phi))
+
+
+def step(g: Grid, phi: np.ndarray, phi_prev: np.ndarray, rho: np.ndarray) -> np.ndarray:
+    rho = np.ascontiguousarray(rho, dtype=np.float64)
+    out = np.zeros(g.ghosted_shape)
+    _L().og_step(ctypes.byref(g._s()), _p(phi), _p(phi_prev), _p(rho), _p(out))
+    return out
+
+
+def run(g: Grid, phi: np.ndarray, phi_prev: np.ndarray, rho: np.ndarray, nsteps: int) -> None:
+    """Advance (phi, phi_prev) in place by nsteps sub-steps."""
+    rho = np.ascontiguousarray(rho, dtype=np.float64)
+    work = np.zeros(g.ghosted_shape)
+    _L().og_run(ctypes.byref(g._s()), _p(phi), _p(phi_prev), _p(rho), int(nsteps), _p(work))
+
+
+def accel(g: Grid, phi: np.ndarray):
+    ax, ay, az = (np.zeros(g.shape) for _ in range(3))
+    _L().og_accel(ctypes.byref(g._s()), _p(phi), _p(ax), _p(ay), _p(az))
+    return ax, ay, az
+
+
+def residual(g: Grid, phi: np.ndarray, rho: np.ndarray):
+    """(rms, max) of Laplacian_h phi - 4 pi G (rho - rho_bar) over the interior."""
+    rho = np.ascontiguousarray(rho, dtype=np.float64)
+    out = np.zeros(2)
+    _L().og_residual(ctypes.byref(g._s()), _p(phi), _p(rho), _p(out))
+    return float(out[0]), float(out[1])
+
+
+def compare(g: Grid, a: np.ndarray, b: np.ndarray):
+    """(rel L2, rel Linf, paper's <dphi~>) of ghosted a against ghosted b over the interior."""
+    out = np.zeros(3)
+    _L().og_compare(ctypes.byref(g._s()), _p(a), _p(b), _p(out))
+    return float(out[0]), float(out[1]), float(out[2])
+
+
+def adjoint(g: Grid, lam_T: np.ndarray, T: int) -> np.ndarray:
+    """dL/drho for L depending on phi^T only, given lam_T = dL/dphi^T (interior array), after T sub-steps."""
+    lam_T = np.ascontiguousarray(lam_T, dtype=np.float64)
+    grad = np.zeros(g.shape)
+    _L().og_adjoint(ctypes.byref(g._s()), _p(lam_T), int(T), _p(grad))
+    return grad
+
+
+# ---- state set-up per boundary condition (initial data as the paper's tests use it: phi = 0 or a seed) -------
+
+def initial_state(g: Grid, rho: np.ndarray, lmax: int = 0, phi0: np.ndarray | None = None,
+                  phi_prev0: np.ndarray | None = None):
+    """Ghosted (phi, phi_prev) at t = 0.  Interior from the seeds (default 0); face ghosts per boundary condition:
+    multipole Dirichlet data of rho, periodic copies, or the Robin static limit of the seeded interior."""
+    phi = ghosted(g, phi0)
+    prev = ghosted(g, phi_prev0 if phi_prev0 is not None else phi0)
+    if g.bc == BC_DIRICHLET:
+        Q = moments(g, rho, lmax)
+        fill_multipole_ghosts(g, lmax, Q, phi)
+        fill_multipole_ghosts(g, lmax, Q, prev)
+    elif g.bc == BC_PERIODIC:
+        fill_periodic_ghosts(g, phi)
+        fill_periodic_ghosts(g, prev)
+    else:
+        fill_robin_static_ghosts(g, phi)
+        fill_robin_static_ghosts(g, prev)
+    return phi, prev
