@@ -1,0 +1,383 @@
+#!/usr/bin/env python
+"""Benchmark of the hyperbolic self-gravity hot path (arXiv 1602.05700) on GB300.
+
+Workload (one "step" = the gravity work of one hydro step, Sec. 2): a 512^3 grid on the unit cube with the
+time-dependent source of two Gaussian blobs (sigma 0.05, mass 1 each) orbiting at radius 0.15 with omega = 2 pi;
+c_h = 10 x the blob speed; hydro step 0.5 h / v_max split into 20 wave sub-steps (rho frozen, Sec. 2); Robin outer
+boundary.  Per step: hg_set_density (rho of that hydro time, resident in HBM), 20 sub-steps, -grad phi.
+
+Metric: Gcell-updates/s = 512^3 x 20 x steps / time (whole job, all ranks), FP32 with compensated increments;
+the FP64 reference mode is measured on the same workload and reported beside it.  `roofline` is the sub-step
+kernel's algorithmic bytes per launch / its CUDA-event duration inside the timed region, against the measured
+copy bandwidth.  `e2e` repeats the measurement through the public API with the density coming from pinned host
+memory and the acceleration copied back every step.  `--impl reference` times the CPU oracle instead.
+
+Multi-GPU: the path has no exchange step in this build (one independent grid per rank), so N ranks run N
+independent problems (weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_SUB = 20
+BYTES_PER_CELL = {"f32k": 28, "f64": 32}  # algorithmic HBM bytes of one sub-step (read 4 / write 3; read 3 / write 1)
+DP_OPS_PER_CELL = 15                      # FP64 instructions of the f64 update (cell.cuh)
+FP64_NOMINAL_TFLOPS = 1.25                # GB300 FP64 (FMA = 2 flops): 0.625 T instructions/s
+FALLBACK_HBM_GBS = 6800.0
+
+
+def workload(n):
+    h = 1.0 / n
+    v_max = 0.15 * 2.0 * math.pi
+    c = 10.0 * v_max
+    dt_hyd = 0.5 * h / v_max
+    return dict(n=n, h=h, v_max=v_max, c=c, dt_hyd=dt_hyd, dt=dt_hyd / N_SUB, origin=(-0.5, -0.5, -0.5), G=1.0)
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def source_hash():
+    """sha256 over the CUDA sources, to tell whether a committed ncu figure was taken on the current kernels."""
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1602_05700_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh")):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()
+
+
+def stencil_traffic(kernel, n):
+    """DRAM bytes per launch (scaled to n^3 cells) from profiles/traffic.json, if taken on the current sources."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    if d.get("csrc_sha256") != source_hash():
+        return None
+    e = d.get("kernels", {}).get(kernel)
+    if not e:
+        return None
+    return round(e["dram_bytes_per_launch"] * (n ** 3) / e["cells"])
+
+
+class Clocks:
+    """nvidia-smi samples during the timed region (SM clock, limits, throttle reasons)."""
+
+    def __init__(self, index):
+        self.path = tempfile.mktemp(suffix=".csv")
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 9:
+                try:
+                    rows.append((float(f[1]), float(f[2]), float(f[3]), f[5:9]))
+                except ValueError:
+                    pass
+        os.unlink(self.path)
+        if not rows:
+            return None
+        load = [r for r in rows if r[2] > 200.0] or rows
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in load for i, v in enumerate(r[3]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in load), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+
+    import paper_1602_05700_gb300 as hg
+    from paper_1602_05700_gb300 import inputs as I
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    W = workload(args.n)
+    n = W["n"]
+    steps, warm = args.steps, args.warmup
+    # densities of consecutive hydro steps, generated before timing and resident in HBM (f32, 0.5 GB each at 512^3)
+    t_off = rank * 0.25  # each rank its own phase of the orbit: independent problems
+    rhos = [I.blob_density_torch(n, I.orbit_blobs(t_off + s * W["dt_hyd"]), dev, torch.float32)
+            for s in range(warm + steps)]
+    hbm_peak, peak_kind = peaks()
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(x):
+        if world == 1:
+            return x
+        import torch.distributed as dist
+        t = torch.tensor([x], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def measure(prec, depth, k_steps, profile_region=False):
+        g = hg.Grid(n, n, n, W["h"], W["origin"], W["c"], W["G"], W["dt"], prec, "robin")
+        if depth > 1:
+            g.set_temporal_depth(depth)
+        out = [torch.empty((n, n, n), device=dev, dtype=torch.float32) for _ in range(3)]
+
+        def one(s):
+            g.set_density(rhos[s % len(rhos)])
+            g.step(N_SUB)
+            g.accel(out=out)
+
+        for s in range(warm):
+            one(s)
+        barrier()
+        g.profile(True)
+        g.profile_read()
+        launches0 = g.profile_read()[2]
+        clocks = Clocks(local_rank) if rank == 0 else None
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        if profile_region:
+            torch.cuda.cudart().cudaProfilerStart()  # lets an external profiler capture just this region
+        e0.record()
+        for s in range(warm, warm + k_steps):
+            one(s)
+        e1.record()
+        barrier()
+        if profile_region:
+            torch.cuda.cudart().cudaProfilerStop()
+        ck = clocks.stop() if clocks else None
+        ms = max_over_ranks(e0.elapsed_time(e1))
+        kern_ms, kern_n, launches1 = g.profile_read()
+        g.profile(False)
+        st = g.stats(check=False)
+        g.free()
+        return dict(ms=ms, kern_ms=kern_ms, kern_n=kern_n, launches=launches1 - launches0, clocks=ck, stats=st,
+                    depth=depth, steps=k_steps)
+
+    cells = n ** 3
+
+    def rate(r):
+        return cells * N_SUB * r["steps"] * world / (r["ms"] * 1e-3) / 1e9
+
+    def roofline(r):
+        avg = r["kern_ms"] / max(r["kern_n"], 1)
+        subs = N_SUB * r["steps"] / max(r["kern_n"], 1)  # sub-steps per launch (the temporal depth)
+        alg = BYTES_PER_CELL["f32k"] * cells  # one read of the state and one write per launch
+        ach = alg / (avg * 1e-3) / 1e9
+        kname = "k_step_f32k" if r["depth"] == 1 else f"k_temporal_f32k<{r['depth']}>"
+        return {"bound": "hbm", "achieved": round(ach, 1), "peak": hbm_peak, "unit": "GB/s",
+                "frac": round(ach / hbm_peak, 4), "peak_kind": f"{peak_kind} copy bandwidth",
+                "traffic": stencil_traffic(kname, n), "kernel": kname, "alg_bytes_per_launch": alg,
+                "substeps_per_launch": round(subs, 3), "avg_launch_ms": round(avg, 5),
+                "effective_single_sweep_gbs": round(ach * subs, 1)}
+
+    # temporal depth: a short sweep picks the fastest depth for the headline measurement
+    if args.depth > 0:
+        best = args.depth
+        sweep = None
+    else:
+        sweep = {}
+        for d in range(1, 5):
+            sweep[d] = round(rate(measure("f32k", d, 3)), 2)
+        best = max(sweep, key=sweep.get)
+    res = measure("f32k", best, steps, profile_region=True)
+    value = rate(res)
+    line = {
+        "metric": "Gcell-updates/s per wave sub-step (512^3, FP32 compensated; FP64 beside it)",
+        "value": round(value, 3), "unit": "Gcell-updates/s", "n_gpus": world, "steps": steps, "warmup": warm,
+        "ms_per_step": round(res["ms"] / steps, 4), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"{n}^3 unit cube, two orbiting Gaussian blobs (sigma 0.05, mass 1, r 0.15, omega 2pi), "
+                               f"Robin boundary, c_h = 10 v_max, {N_SUB} sub-steps per hydro step; per step "
+                               "set_density + 20 sub-steps + -grad phi",
+                   "grid": [n, n, n], "substeps_per_step": N_SUB, "precision": "f32 compensated (Kahan)",
+                   "temporal_depth": best, "depth_sweep_gcells": sweep,
+                   "parallelism": f"{world} independent grids (one per GPU)",
+                   "l2": f"working set {6 * 4 * cells / 1e9:.1f} GB per grid >> 129 MB L2 (no flush needed)"},
+        "roofline": roofline(res),
+        "gpu_launches": res["launches"],
+        "clocks": res["clocks"],
+    }
+    if best != 1:
+        r1 = measure("f32k", 1, max(3, steps // 2))
+        line["single_sweep"] = {"value": round(rate(r1), 3), "unit": "Gcell-updates/s", "steps": r1["steps"],
+                                "roofline": roofline(r1)}
+    # FP64 reference mode on the same workload
+    if not args.skip_fp64:
+        k64 = max(2, steps // 4)
+        r64 = measure("f64", 1, k64)
+        v64 = cells * N_SUB * k64 * world / (r64["ms"] * 1e-3) / 1e9
+        avg64 = r64["kern_ms"] / max(r64["kern_n"], 1)
+        hbm64 = BYTES_PER_CELL["f64"] * cells / (avg64 * 1e-3) / 1e9
+        dp = DP_OPS_PER_CELL * cells / (avg64 * 1e-3) / 1e9
+        line["fp64"] = {"value": round(v64, 3), "unit": "Gcell-updates/s", "steps": k64,
+                        "ms_per_step": round(r64["ms"] / k64, 4),
+                        "roofline": {"bound": "alu", "achieved": round(dp, 1), "peak": FP64_NOMINAL_TFLOPS * 1e3 / 2,
+                                     "unit": "G FP64-instr/s", "frac": round(dp / (FP64_NOMINAL_TFLOPS * 1e3 / 2), 4),
+                                     "peak_kind": "nominal FP64 rate (1.25 TFLOP/s, FMA = 2)",
+                                     "hbm_achieved_gbs": round(hbm64, 1),
+                                     "hbm_frac": round(hbm64 / hbm_peak, 4), "kernel": "k_step_f64",
+                                     "avg_launch_ms": round(avg64, 5)},
+                        "gpu_launches": r64["launches"]}
+    # end to end through the public API: density from pinned host memory, acceleration back to the host
+    if not args.skip_e2e:
+        ke = max(2, min(steps, 5))
+        host_rho = [rhos[s].cpu().pin_memory() for s in range(min(2, len(rhos)))]
+        host_acc = [torch.empty((n, n, n), dtype=torch.float32).pin_memory() for _ in range(3)]
+        g = hg.Grid(n, n, n, W["h"], W["origin"], W["c"], W["G"], W["dt"], "f32k", "robin")
+        if best > 1:
+            g.set_temporal_depth(best)
+        out = [torch.empty((n, n, n), device=dev, dtype=torch.float32) for _ in range(3)]
+
+        def e2e_step(s):
+            g.set_density(host_rho[s % len(host_rho)])
+            g.step(N_SUB)
+            g.accel(out=out)
+            for a, b in zip(host_acc, out):
+                a.copy_(b, non_blocking=True)
+            torch.cuda.current_stream().synchronize()
+
+        for s in range(2):
+            e2e_step(s)
+        barrier()
+        t0 = time.perf_counter()
+        for s in range(ke):
+            e2e_step(s)
+        barrier()
+        sec = max_over_ranks(time.perf_counter() - t0)
+        g.free()
+        line["e2e"] = {"value": round(cells * N_SUB * ke * world / sec / 1e9, 3), "unit": "Gcell-updates/s",
+                       "h2d_bytes_per_step": 4 * cells, "d2h_bytes_per_step": 12 * cells, "steps": ke,
+                       "temporal_depth": best,
+                       "note": "pinned host density in, pinned host -grad phi out, every step"}
+    if rank == 0 and not args.skip_cpu:
+        line["cpu_baseline"] = cpu_baseline(args.n, args.cpu_substeps)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return line
+
+
+def cpu_baseline(n, substeps):
+    """The oracle as it stands (single-threaded C), on the same grid and source, a bounded number of sub-steps."""
+    import numpy as np
+
+    import oracle as O
+    from paper_1602_05700_gb300 import inputs as I
+
+    W = workload(n)
+    g = O.Grid(n, n, n, W["h"], W["origin"], W["c"], W["G"], W["dt"], O.BC_ROBIN)
+    rho = I.blob_density(n, I.orbit_blobs(0.0))
+    p, q = O.initial_state(g, rho)
+    O.build()
+    t0 = time.perf_counter()
+    O.run(g, p, q, rho, substeps)
+    sec = time.perf_counter() - t0
+    del p, q, rho
+    return {"value": round(n ** 3 * substeps / sec / 1e9, 5), "unit": "Gcell-updates/s", "cores": 1, "kind": "oracle",
+            "sample": f"{n}^3 grid, same Robin/orbiting-blob workload, {substeps} sub-steps ({sec:.1f} s), "
+                      "single-threaded C oracle (oracle/hg_oracle.c)"}
+
+
+def run_reference(args):
+    """The CPU oracle timed as the reference arm: each step a bounded sample (a few sub-steps of the workload)."""
+    import numpy as np  # noqa: F401
+
+    import oracle as O
+    from paper_1602_05700_gb300 import inputs as I
+
+    W = workload(args.n)
+    n = W["n"]
+    g = O.Grid(n, n, n, W["h"], W["origin"], W["c"], W["G"], W["dt"], O.BC_ROBIN)
+    O.build()
+    sub = args.ref_substeps
+    rho = I.blob_density(n, I.orbit_blobs(0.0))
+    p, q = O.initial_state(g, rho)
+    for _ in range(args.warmup):
+        O.run(g, p, q, rho, 1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        O.run(g, p, q, rho, sub)
+    sec = time.perf_counter() - t0
+    v = n ** 3 * sub * args.steps / sec / 1e9
+    sample = (f"{n}^3 grid, same Robin/orbiting-blob workload, {sub} sub-step(s) per step (a bounded sample of the "
+              f"{N_SUB}-sub-step hydro step), single-threaded C oracle")
+    return {"impl": "reference", "metric": "Gcell-updates/s per wave sub-step (512^3, FP32 compensated; FP64 beside it)",
+            "value": round(v, 5), "unit": "Gcell-updates/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(sec / args.steps * 1e3, 3), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{n}^3 unit cube, two orbiting Gaussian blobs, Robin boundary (oracle sample)",
+                       "grid": [n, n, n]},
+            "cpu_baseline": {"value": round(v, 5), "unit": "Gcell-updates/s", "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": round(v, 5), "unit": "Gcell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=512)
+    ap.add_argument("--depth", type=int, default=0,
+                    help="sub-steps fused per pass (temporal blocking); 0 = pick the fastest of 1..4 by a short sweep")
+    ap.add_argument("--skip-fp64", action="store_true")
+    ap.add_argument("--skip-e2e", action="store_true")
+    ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--cpu-substeps", type=int, default=6)
+    ap.add_argument("--ref-substeps", type=int, default=1)
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps(run_reference(args)), flush=True)
+        return
+    import paper_1602_05700_gb300 as hg
+    hg.build()
+    line = run_ours(args, rank, world, local_rank)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,176 @@
+/*
+ * hg.h -- C ABI of the GB300 (sm_103a) hyperbolic self-gravity library.
+ *
+ * The library advances the wave-equation replacement of Poisson's equation (arXiv 1602.05700, Sec. 1,
+ * Eq. HNeq.)
+ *
+ *     (-1/c_h^2 d^2/dt^2 + Laplacian) phi = 4 pi G rho
+ *
+ * by explicit sub-steps on a uniform Cartesian grid (Sec. 2: "simple discretization", wave sub-steps on their own
+ * time-line with rho frozen, c_h = k_g (c_s + |v|) chosen by the caller), with the outer boundary conditions of
+ * Sec. 2 and Sec. 4 (Robin / monopole radiation, Dirichlet by multipole expansion, periodic with the mean density
+ * removed), and returns the gravitational acceleration -grad phi that a hydro code consumes.
+ *
+ * Discretisation (the paper leaves it open; this is the library's reading):
+ *   cell-centred cells of side h, cell (i,j,k) centred at origin + (i+1/2, j+1/2, k+1/2) h, one ghost layer;
+ *   nu = c_h dt / h;
+ *   phi^{n+1} = 2 phi^n - phi^{n-1} + nu^2 sum_{6 nb}(phi^n_nb - phi^n) - (c_h dt)^2 4 pi G (rho - rho_bar),
+ *   rho_bar = mean(rho) with periodic boundaries, else 0; phi^0 = phi^{-1} = 0 unless seeded.
+ *   Stable for nu sqrt(3) <= 1 (checked by hg_init_grid).
+ *
+ * Conventions for every entry point:
+ *   - Return value: HG_OK (0) or a negative HG_ERR_* code; hg_last_error() then gives a message (thread-local).
+ *     No call aborts, traps or waits without bound.
+ *   - Array arguments are plain pointers.  Unless stated otherwise an array is nz*ny*nx elements in C order
+ *     (z slowest, x fastest), no padding, of the element type given by a dtype argument (HG_DT_F32 = float,
+ *     HG_DT_F64 = double).  A flag *_on_device says whether a pointer is device memory of the grid's device
+ *     (1) or host memory (0).  The caller owns every pointer it passes; the library copies what it keeps.
+ *   - All device work is enqueued on the CUDA stream given to hg_init_grid.  Calls that return data to host
+ *     memory synchronise that stream; hg_step and the device-to-device calls do not.
+ *   - A grid is used from one host thread at a time.
+ */
+#ifndef HG_H
+#define HG_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define HG_OK 0
+#define HG_ERR_ARG (-1)       /* invalid argument (null pointer, bad size, unknown enum, ...) */
+#define HG_ERR_CFL (-2)       /* time step violates nu sqrt(3) <= 1, or the Robin boundary's nu/mu <= 1 */
+#define HG_ERR_CUDA (-3)      /* a CUDA runtime call failed; the message names it */
+#define HG_ERR_NONFINITE (-4) /* a NaN or Inf was found in the state (hg_get_stats) */
+#define HG_ERR_TIMEOUT (-5)   /* a bounded device-side wait gave up */
+#define HG_ERR_STATE (-6)     /* call not valid in the grid's current state */
+
+/* storage / arithmetic precision of a grid's state */
+#define HG_PREC_F32K 0 /* float storage, compensated (Kahan-style) increments of phi */
+#define HG_PREC_F64 1  /* double storage and arithmetic: the reference mode */
+
+/* element type of caller buffers */
+#define HG_DT_F32 0
+#define HG_DT_F64 1
+
+/* outer boundary conditions (Sec. 2 and Sec. 4) */
+#define HG_BC_DIRICHLET_ANALYTIC 0  /* ghost phi = -G M / r, M = sum rho h^3 (monopole of the density) */
+#define HG_BC_DIRICHLET_MULTIPOLE 1 /* ghost phi from the multipole expansion of rho up to l = lmax */
+#define HG_BC_ROBIN 2               /* monopole radiation condition d_t(r phi) + c_h d_r(r phi) = 0 */
+#define HG_BC_PERIODIC 3            /* wrap-around; the source uses rho - mean(rho) */
+
+#define HG_MAX_LMAX 8
+
+typedef struct hg_grid hg_grid;
+
+/* FP64 diagnostics of the current state (Sec. 4, Eq. error, and the steady-state check of Eq. Poissoneq.). */
+typedef struct {
+    double mass;           /* sum rho h^3 over the interior (as stored) */
+    double residual_rms;   /* rms over the interior of Laplacian_h phi^n - 4 pi G (rho - rho_bar) */
+    double residual_max;   /* max of |...| */
+    double change_rel;     /* ||phi^n - phi^{n-1}||_2 / ||phi^n||_2 over the interior */
+    double phi_max;        /* max |phi^n| over the interior */
+    long long step;        /* sub-steps taken since the last hg_set_phi / hg_init_grid */
+    int nonfinite;         /* 1 if a NaN or Inf was seen in phi^n, phi^{n-1} or rho */
+} hg_stats;
+
+/*
+ * Create a grid of nx*ny*nz cells of side h whose lower corner is origin[3] (so cell centres are at
+ * origin + (idx + 1/2) h).  c_h is the gravity wave speed (Sec. 2: c_g = k_g (c_s + |v|)), G the gravitational
+ * constant, dt the sub-step.  precision is HG_PREC_*, bc is HG_BC_*, lmax the multipole order for
+ * HG_BC_DIRICHLET_MULTIPOLE (0..HG_MAX_LMAX; ignored otherwise).  cuda_stream is a cudaStream_t (NULL = the
+ * legacy default stream) on the current device; all later work of this grid goes there.
+ * phi^0 = phi^{-1} = 0 and rho = 0 on return.  Errors: HG_ERR_ARG (sizes < 1, h/c_h/dt <= 0, bad enum),
+ * HG_ERR_CFL (nu sqrt(3) > 1; for Robin also any ghost with nu/mu > 1, i.e. the domain must surround the
+ * origin), HG_ERR_CUDA (allocation).  On error *g is NULL.
+ */
+int hg_init_grid(hg_grid** g, int nx, int ny, int nz, double h, const double origin[3], double c_h, double G,
+                 double dt, int precision, int bc, int lmax, void* cuda_stream);
+
+/*
+ * Set the density (Sec. 2: rho is frozen during the wave sub-steps of one hydro step).  rho: nz*ny*nx values of
+ * type dtype, host or device.  Recomputes the FP64 mass, the mean (periodic) and, for the Dirichlet modes, the
+ * FP64 multipole moments and the ghost values of phi^n and phi^{n-1} (Sec. 4, Dirichlet boundary by multipole
+ * expansion).  The interior of phi is not touched.
+ */
+int hg_set_density(hg_grid* g, const void* rho, int dtype, int on_device);
+
+/*
+ * Seed the state: phi^n = phi, phi^{n-1} = phi_prev (phi_prev may be NULL: then phi^{n-1} = phi^n, i.e. zero
+ * initial time derivative).  Sec. 2 seeds phi from a Poisson solve.  Ghosts are set per boundary condition:
+ * Dirichlet data, periodic copies, or the Robin static limit r_g phi_g = r_i phi_i.  Resets the step count.
+ */
+int hg_set_phi(hg_grid* g, const void* phi, const void* phi_prev, int dtype, int on_device);
+
+/* Advance n_substeps >= 0 sub-steps.  Asynchronous on the grid's stream. */
+int hg_step(hg_grid* g, int n_substeps);
+
+/*
+ * Number of sub-steps fused per pass over the grid in hg_step: 1 = one sweep per sub-step (default); k in
+ * 2..HG_MAX_TEMPORAL_DEPTH advances k sub-steps per round trip through HBM (rho is frozen across them, Sec. 2).
+ * Results are the same as k single sweeps.  HG_ERR_ARG for k out of range.
+ */
+#define HG_MAX_TEMPORAL_DEPTH 4
+int hg_set_temporal_depth(hg_grid* g, int k);
+
+/*
+ * Gravitational acceleration a = -grad phi^n by second-order central differences, ghosts supplying the face
+ * values.  ax, ay, az: device buffers of nz*ny*nx elements of type dtype.  Asynchronous.
+ */
+int hg_accel(hg_grid* g, void* ax, void* ay, void* az, int dtype);
+
+/* Copy phi^n (interior) into out: nz*ny*nx elements of type dtype, host or device.  For HG_PREC_F32K with
+ * dtype HG_DT_F64 the compensated value (float + its compensation, summed in double) is returned. */
+int hg_get_phi(hg_grid* g, void* out, int dtype, int on_device);
+
+/* Copy phi^n including its face ghosts into out: (nz+2)*(ny+2)*(nx+2) doubles in host memory, C order,
+ * interior cell (i,j,k) at ((k+1)(ny+2) + j+1)(nx+2) + i+1; edge and corner entries are 0. */
+int hg_get_phi_ghosted(hg_grid* g, double* out);
+
+/* FP64 diagnostics of the current state (synchronises the stream).  Returns HG_ERR_NONFINITE (with *s filled)
+ * when a NaN or Inf is present. */
+int hg_get_stats(hg_grid* g, hg_stats* s);
+
+/* The FP64 multipole moments Q_lm = sum rho h^3 r^l Y_lm (real orthonormal Y_lm about the coordinate origin),
+ * (lmax+1)^2 doubles at index l*l + l + m, of the last hg_set_density (HG_ERR_STATE unless a Dirichlet mode). */
+int hg_get_moments(hg_grid* g, double* Q);
+
+/*
+ * Compare phi^n with a reference potential phi_P (Sec. 4, Eq. error): out[0] = ||phi - phi_P||_2 / ||phi_P||_2,
+ * out[1] = max|phi - phi_P| / max|phi_P|, out[2] = the paper's average relative error
+ * sqrt(mean(((phi - phi_P) / phi_P)^2)).  phi_P: nz*ny*nx doubles, host or device.
+ */
+int hg_compare(hg_grid* g, const double* phi_P, int on_device, double out[3]);
+
+/* Checkpoint / resume of the full state (bit-exact): hg_state_bytes gives the size of the opaque host buffer
+ * that hg_save_state fills and hg_load_state reads. */
+size_t hg_state_bytes(const hg_grid* g);
+int hg_save_state(hg_grid* g, void* host_buf);
+int hg_load_state(hg_grid* g, const void* host_buf);
+
+/*
+ * Measurement hooks.  hg_profile(g, 1) makes the library record a pair of CUDA events on the grid's stream around
+ * every launch of its sub-step kernel (the single-sweep or the temporally blocked stencil); hg_profile(g, 0) stops.
+ * hg_profile_read synchronises the stream and returns the summed duration (ms) and the number of those timed
+ * launches since the previous read (then resets both), and the total number of kernels the library has launched
+ * for this grid since its creation.  Any output pointer may be NULL.
+ */
+int hg_profile(hg_grid* g, int enable);
+int hg_profile_read(hg_grid* g, double* substep_kernel_ms, long long* substep_launches, long long* kernel_launches);
+
+/* Block until the grid's stream is idle; HG_ERR_CUDA carries any pending asynchronous error. */
+int hg_sync(hg_grid* g);
+
+/* Release the grid and its device memory (NULL is allowed). */
+void hg_free(hg_grid* g);
+
+/* Message of the last failing call on this host thread ("" if none). */
+const char* hg_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HG_H */

@@ -1,0 +1,220 @@
+"""Python binding of the GB300 hyperbolic self-gravity library (arXiv 1602.05700).
+
+A thin layer over the C ABI of include/hg.h: it turns tensors and arrays into pointers, sizes and flags.  Every
+step of the method runs in the CUDA kernels of ``csrc/``; PyTorch only provides device memory and streams.
+
+    import torch, paper_1602_05700_gb300 as hg
+    g = hg.Grid.unit_cube(256, c=1.0, G=1.0, cfl=0.5, precision="f32k", bc="robin")
+    g.set_density(rho)           # (nz, ny, nx) tensor or array, rho frozen over the sub-steps (Sec. 2)
+    g.step(20)                   # k_g wave sub-steps per hydro step (Sec. 2)
+    ax, ay, az = g.accel()       # -grad phi for the hydro step
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _lib
+from ._lib import (HG_BC_DIRICHLET_ANALYTIC, HG_BC_DIRICHLET_MULTIPOLE, HG_BC_PERIODIC, HG_BC_ROBIN, HG_DT_F32,
+                   HG_DT_F64, HG_MAX_LMAX, HG_MAX_TEMPORAL_DEPTH, HG_PREC_F32K, HG_PREC_F64, HGError)
+
+BC = {"dirichlet": HG_BC_DIRICHLET_ANALYTIC, "dirichlet_analytic": HG_BC_DIRICHLET_ANALYTIC,
+      "multipole": HG_BC_DIRICHLET_MULTIPOLE, "dirichlet_multipole": HG_BC_DIRICHLET_MULTIPOLE,
+      "robin": HG_BC_ROBIN, "periodic": HG_BC_PERIODIC}
+PREC = {"f32k": HG_PREC_F32K, "f64": HG_PREC_F64}
+
+__all__ = ["Grid", "HGError", "BC", "PREC", "build"]
+
+
+def build(force: bool = False) -> str:
+    from .build import build as _b
+    return _b(force=force)
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _buffer(x, want_dtype=None):
+    """(pointer, dtype code, on_device, keepalive) for a torch tensor or numpy array holding nz*ny*nx values."""
+    try:
+        torch = _torch()
+        is_tensor = isinstance(x, torch.Tensor)
+    except ImportError:  # pragma: no cover
+        is_tensor = False
+    if is_tensor:
+        t = x
+        if t.dtype not in (torch.float32, torch.float64):
+            t = t.to(torch.float64)
+        t = t.contiguous()
+        code = HG_DT_F64 if t.dtype == torch.float64 else HG_DT_F32
+        return ctypes.c_void_p(t.data_ptr()), code, 1 if t.is_cuda else 0, t
+    a = np.asarray(x)
+    if a.dtype not in (np.float32, np.float64):
+        a = a.astype(np.float64)
+    a = np.ascontiguousarray(a)
+    code = HG_DT_F64 if a.dtype == np.float64 else HG_DT_F32
+    return ctypes.c_void_p(a.ctypes.data), code, 0, a
+
+
+class Grid:
+    """One grid of nx*ny*nz cells of side h (lower corner `origin`), wave speed c, constant G, sub-step dt."""
+
+    def __init__(self, nx, ny, nz, h, origin, c, G, dt, precision="f32k", bc="robin", lmax=0, stream=None):
+        torch = _torch()
+        L = _lib.lib()
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self._stream = stream
+        handle = ctypes.c_void_p()
+        org = (ctypes.c_double * 3)(*[float(o) for o in origin])
+        prec = PREC[precision] if isinstance(precision, str) else int(precision)
+        bcc = BC[bc] if isinstance(bc, str) else int(bc)
+        _lib.check(L.hg_init_grid(ctypes.byref(handle), int(nx), int(ny), int(nz), float(h), org, float(c), float(G),
+                                  float(dt), prec, bcc, int(lmax), ctypes.c_void_p(stream.cuda_stream)))
+        self._h = handle
+        self.nx, self.ny, self.nz, self.h = int(nx), int(ny), int(nz), float(h)
+        self.origin = tuple(float(o) for o in origin)
+        self.c, self.G, self.dt = float(c), float(G), float(dt)
+        self.precision, self.bc, self.lmax = prec, bcc, int(lmax)
+        self.device = torch.device("cuda", torch.cuda.current_device())
+
+    @classmethod
+    def unit_cube(cls, n, c=1.0, G=1.0, cfl=0.5, precision="f32k", bc="robin", lmax=0, ny=None, nz=None, stream=None):
+        """n cells per side of [-1/2, 1/2] (h = 1/n), dt = cfl h / (c sqrt 3)."""
+        h = 1.0 / n
+        return cls(n, ny or n, nz or n, h, (-0.5, -0.5, -0.5), c, G, cfl * h / (c * np.sqrt(3.0)), precision, bc,
+                   lmax, stream)
+
+    @property
+    def shape(self):
+        return (self.nz, self.ny, self.nx)
+
+    @property
+    def handle(self):
+        if self._h is None:
+            raise HGError(-1, "grid was freed")
+        return self._h
+
+    def set_density(self, rho):
+        p, code, dev, keep = _buffer(rho)
+        self._check_size(keep)
+        _lib.check(_lib.lib().hg_set_density(self.handle, p, code, dev))
+
+    def set_phi(self, phi, phi_prev=None):
+        p, code, dev, keep = _buffer(phi)
+        self._check_size(keep)
+        if phi_prev is not None:
+            q, code2, dev2, keep2 = _buffer(phi_prev, code)
+            self._check_size(keep2)
+            if code2 != code or dev2 != dev:
+                raise HGError(-1, "phi and phi_prev must have the same dtype and device")
+        else:
+            q, keep2 = ctypes.c_void_p(0), None
+        _lib.check(_lib.lib().hg_set_phi(self.handle, p, q, code, dev))
+
+    def step(self, n=1):
+        _lib.check(_lib.lib().hg_step(self.handle, int(n)))
+
+    def set_temporal_depth(self, k):
+        _lib.check(_lib.lib().hg_set_temporal_depth(self.handle, int(k)))
+
+    def accel(self, dtype=None, out=None):
+        """-grad phi^n as three (nz, ny, nx) device tensors (written into `out` when given)."""
+        torch = _torch()
+        if out is None:
+            dtype = dtype or (torch.float64 if self.precision == HG_PREC_F64 else torch.float32)
+            out = [torch.empty(self.shape, dtype=dtype, device=self.device) for _ in range(3)]
+        else:
+            dtype = out[0].dtype
+            for t in out:
+                if not (t.is_cuda and t.is_contiguous() and t.dtype == dtype and tuple(t.shape) == self.shape):
+                    raise HGError(-1, "accel outputs must be contiguous device tensors of the grid shape, one dtype")
+        code = HG_DT_F64 if dtype == torch.float64 else HG_DT_F32
+        _lib.check(_lib.lib().hg_accel(self.handle, *[ctypes.c_void_p(t.data_ptr()) for t in out], code))
+        return tuple(out)
+
+    def phi(self, dtype=None, device="cuda"):
+        """phi^n on the interior as an (nz, ny, nx) tensor (device) or numpy array (device='cpu')."""
+        torch = _torch()
+        dtype = dtype or torch.float64
+        code = HG_DT_F64 if dtype == torch.float64 else HG_DT_F32
+        if device == "cpu":
+            out = np.empty(self.shape, dtype=np.float64 if code == HG_DT_F64 else np.float32)
+            _lib.check(_lib.lib().hg_get_phi(self.handle, ctypes.c_void_p(out.ctypes.data), code, 0))
+            return out
+        out = torch.empty(self.shape, dtype=dtype, device=self.device)
+        _lib.check(_lib.lib().hg_get_phi(self.handle, ctypes.c_void_p(out.data_ptr()), code, 1))
+        return out
+
+    def phi_ghosted(self) -> np.ndarray:
+        out = np.empty((self.nz + 2, self.ny + 2, self.nx + 2))
+        _lib.check(_lib.lib().hg_get_phi_ghosted(self.handle, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+        return out
+
+    def stats(self, check=True) -> dict:
+        s = _lib.hg_stats()
+        rc = _lib.lib().hg_get_stats(self.handle, ctypes.byref(s))
+        if check:
+            _lib.check(rc)
+        return {k: getattr(s, k) for k, _ in _lib.hg_stats._fields_} | {"rc": rc}
+
+    def moments(self) -> np.ndarray:
+        nq = (self.lmax + 1) ** 2 if self.bc == HG_BC_DIRICHLET_MULTIPOLE else 1
+        out = np.zeros(nq)
+        _lib.check(_lib.lib().hg_get_moments(self.handle, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+        return out
+
+    def compare(self, phi_P):
+        """(rel L2, rel Linf, the paper's <dphi~>) of phi^n against a reference potential (Sec. 4)."""
+        torch = _torch()
+        if isinstance(phi_P, torch.Tensor):
+            t = phi_P.to(torch.float64).contiguous()
+            p, dev, keep = ctypes.c_void_p(t.data_ptr()), 1 if t.is_cuda else 0, t
+        else:
+            keep = np.ascontiguousarray(phi_P, dtype=np.float64)
+            p, dev = ctypes.c_void_p(keep.ctypes.data), 0
+        self._check_size(keep)
+        out = (ctypes.c_double * 3)()
+        _lib.check(_lib.lib().hg_compare(self.handle, p, dev, out))
+        return float(out[0]), float(out[1]), float(out[2])
+
+    def save_state(self) -> bytes:
+        n = _lib.lib().hg_state_bytes(self.handle)
+        buf = ctypes.create_string_buffer(n)
+        _lib.check(_lib.lib().hg_save_state(self.handle, buf))
+        return buf.raw
+
+    def load_state(self, blob: bytes) -> None:
+        buf = ctypes.create_string_buffer(blob, len(blob))
+        _lib.check(_lib.lib().hg_load_state(self.handle, buf))
+
+    def profile(self, enable=True):
+        _lib.check(_lib.lib().hg_profile(self.handle, 1 if enable else 0))
+
+    def profile_read(self):
+        """(sub-step kernel ms, timed launches, total kernel launches) since the last read."""
+        ms, n, tot = ctypes.c_double(), ctypes.c_longlong(), ctypes.c_longlong()
+        _lib.check(_lib.lib().hg_profile_read(self.handle, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(tot)))
+        return ms.value, n.value, tot.value
+
+    def sync(self):
+        _lib.check(_lib.lib().hg_sync(self.handle))
+
+    def free(self):
+        if getattr(self, "_h", None) is not None:
+            _lib.lib().hg_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    def _check_size(self, a):
+        n = a.numel() if hasattr(a, "numel") else a.size
+        if n != self.nx * self.ny * self.nz:
+            raise HGError(-1, f"array has {n} values, grid has {self.nx * self.ny * self.nz} cells")

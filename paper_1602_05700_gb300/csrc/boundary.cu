@@ -1,0 +1,309 @@
+// Outer boundary of the hyperbolic gravity solver (arXiv 1602.05700, Sec. 2 and Sec. 4) and the FP64 multipole
+// moments of the density.  Only the six face ghost layers are used: the 7-point stencil and the central
+// gradient never read edge or corner ghosts.
+//
+//   Dirichlet (multipole)   phi_g = -G sum_{l<=lmax} 4 pi/(2l+1) sum_m Q_lm r_g^l Y_lm(x_g) / r_g^{2l+1},
+//                           Q_lm = sum_cells rho h^3 r^l Y_lm(x), about the coordinate origin; lmax = 0 is the
+//                           monopole -G M / r (the analytic mode).  Written once per hg_set_density into both
+//                           time levels (rho, hence the data, is frozen during the sub-steps, Sec. 2).
+//   Robin                   monopole radiation condition d_t(r phi) + c_h d_r(r phi) = 0, d_r = d_n / mu,
+//                           mu = |x_g . n| / r_g, upwinded from the interior neighbour i:
+//                           phi_g^{n+1} = alpha phi_g^n + beta phi_i^n, alpha = 1 - nu/mu, beta = (nu/mu) r_i / r_g.
+//                           Its static limit r_g phi_g = r_i phi_i (gamma = r_i / r_g) seeds a new state.  The
+//                           per-sub-step update is fused into the sweep kernels (stencil.cu, temporal.cu).
+//   Periodic                ghost = interior cell on the opposite face; the sweep kernels write these copies, the
+//                           kernel here fills them for a freshly seeded state.
+//
+// r^l Y_lm is evaluated as a polynomial (no trigonometry): with C_m + i S_m = (x + i y)^m,
+//   r^l Y_lm = n_lm q_l^m(z, r^2) {C_m (m > 0), 1 (m = 0), S_|m| (m < 0)},
+//   q_m^m = (-1)^m (2m-1)!!,  q_{m+1}^m = (2m+1) z q_m^m,
+//   q_l^m = ((2l-1) z q_{l-1}^m - (l+m-1) r^2 q_{l-2}^m) / (l - m),
+// n_l0 = K_l0, n_lm = sqrt(2) K_lm, K_lm = sqrt((2l+1)/(4 pi) (l-m)!/(l+m)!)  (real orthonormal harmonics with the
+// Condon-Shortley phase).
+#include <math.h>
+
+#include "cell.cuh"
+#include "hg_internal.cuh"
+
+namespace hg {
+
+namespace {
+
+template <int LMAX>
+__device__ __forceinline__ void solid_harmonics(double x, double y, double z, const YlmNorm& N,
+                                                double R[(LMAX + 1) * (LMAX + 1)]) {
+    double C[LMAX + 1], S[LMAX + 1];
+    C[0] = 1.0;
+    S[0] = 0.0;
+#pragma unroll
+    for (int m = 1; m <= LMAX; ++m) {
+        C[m] = x * C[m - 1] - y * S[m - 1];
+        S[m] = x * S[m - 1] + y * C[m - 1];
+    }
+    const double r2 = x * x + y * y + z * z;
+    double dfact = 1.0;  // (-1)^m (2m-1)!!
+#pragma unroll
+    for (int m = 0; m <= LMAX; ++m) {
+        if (m > 0) dfact *= -(2.0 * m - 1.0);
+        double q2 = 0.0, q1 = dfact;  // q_{l-2}^m, q_{l-1}^m
+#pragma unroll
+        for (int l = m; l <= LMAX; ++l) {
+            double q;
+            if (l == m) {
+                q = dfact;
+            } else if (l == m + 1) {
+                q = (2.0 * m + 1.0) * z * dfact;
+            } else {
+                q = ((2.0 * l - 1.0) * z * q1 - (double)(l + m - 1) * r2 * q2) * N.inv_lm[l * l + l + m];
+            }
+            if (l > m) {
+                q2 = q1;
+                q1 = q;
+            }
+            const int base = l * l + l;
+            if (m == 0) {
+                R[base] = N.n[base] * q;
+            } else {
+                R[base + m] = N.n[base + m] * q * C[m];
+                R[base - m] = N.n[base + m] * q * S[m];
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ double load_as_double(const void* p, int dtype, long long i) {
+    return dtype == HG_DT_F64 ? ((const double*)p)[i] : (double)((const float*)p)[i];
+}
+
+
+template <int LMAX>
+__global__ void __launch_bounds__(kRedThreads) k_moments(const void* rho, int dtype, int nx, int ny, int nz, double h,
+                                                         double ox, double oy, double oz, YlmNorm N,
+                                                         double* partial) {
+    constexpr int NQ = (LMAX + 1) * (LMAX + 1);
+    __shared__ double sh[32];
+    double acc[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) acc[q] = 0.0;
+    const long long n = (long long)nx * ny * nz;
+    const double h3 = h * h * h;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(c % nx);
+        const long long r = c / nx;
+        const int j = (int)(r % ny);
+        const int k = (int)(r / ny);
+        const double m = load_as_double(rho, dtype, c) * h3;
+        if (m == 0.0) continue;
+        double R[NQ];
+        solid_harmonics<LMAX>(ox + (i + 0.5) * h, oy + (j + 0.5) * h, oz + (k + 0.5) * h, N, R);
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) acc[q] = fma(m, R[q], acc[q]);
+    }
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        double s = block_sum(acc[q], sh);
+        if (threadIdx.x == 0) partial[(long long)blockIdx.x * NQ + q] = s;
+    }
+}
+
+// sum partial[b * nq + q] over b in a fixed order (one block)
+__global__ void __launch_bounds__(kRedThreads) k_finish(const double* partial, int nblocks, int nq, double* out) {
+    __shared__ double sh[32];
+    for (int q = 0; q < nq; ++q) {
+        double v = 0.0;
+        for (int b = threadIdx.x; b < nblocks; b += blockDim.x) v += partial[(long long)b * nq + q];
+        v = block_sum(v, sh);
+        if (threadIdx.x == 0) out[q] = v;
+    }
+}
+
+template <int LMAX>
+__device__ double multipole_phi(double x, double y, double z, const double* Q, const YlmNorm& N, double G) {
+    constexpr int NQ = (LMAX + 1) * (LMAX + 1);
+    double R[NQ];
+    solid_harmonics<LMAX>(x, y, z, N, R);
+    const double r2 = x * x + y * y + z * z;
+    const double ir = 1.0 / sqrt(r2);
+    const double ir2 = ir * ir;
+    double irp = ir;  // r^{-(2l+1)}
+    double phi = 0.0;
+#pragma unroll
+    for (int l = 0; l <= LMAX; ++l) {
+        double s = 0.0;
+#pragma unroll
+        for (int m = -l; m <= l; ++m) s = fma(Q[l * l + l + m], R[l * l + l + m], s);
+        phi = fma(4.0 * 3.14159265358979323846 / (2.0 * l + 1.0) * irp, s, phi);
+        irp *= ir2;
+    }
+    return -G * phi;
+}
+
+struct QArr {
+    double q[kMaxQ];
+};
+
+// write value v (double) into the face ghost q of both time levels
+__device__ __forceinline__ void put_ghost(int prec, void* p0, void* p1, void* l0, void* l1, long long q, double v) {
+    if (prec == HG_PREC_F64) {
+        ((double*)p0)[q] = v;
+        ((double*)p1)[q] = v;
+    } else {
+        float hi, lo;
+        split_f32(v, hi, lo);
+        ((float*)p0)[q] = hi;
+        ((float*)p1)[q] = hi;
+        ((float*)l0)[q] = lo;
+        ((float*)l1)[q] = lo;
+    }
+}
+
+template <int LMAX>
+__global__ void k_dirichlet(int prec, void* p0, void* p1, void* l0, void* l1, Layout L, Faces F, double h, double ox,
+                            double oy, double oz, double G, QArr Q, YlmNorm N) {
+    long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= F.off[6]) return;
+    int gc[3], ic[3];
+    face_cell(F, L.nx, L.ny, L.nz, t, gc, ic);
+    double v = multipole_phi<LMAX>(ox + (gc[0] + 0.5) * h, oy + (gc[1] + 0.5) * h, oz + (gc[2] + 0.5) * h, Q.q, N, G);
+    put_ghost(prec, p0, p1, l0, l1, L.at(gc[0], gc[1], gc[2]), v);
+}
+
+__device__ __forceinline__ double read_phi(int prec, const void* p, const void* lo, long long q) {
+    if (prec == HG_PREC_F64) return ((const double*)p)[q];
+    return join_f32(((const float*)p)[q], ((const float*)lo)[q]);
+}
+__device__ __forceinline__ void write_phi(int prec, void* p, void* lo, long long q, double v) {
+    if (prec == HG_PREC_F64) {
+        ((double*)p)[q] = v;
+    } else {
+        float hi, l;
+        split_f32(v, hi, l);
+        ((float*)p)[q] = hi;
+        ((float*)lo)[q] = l;
+    }
+}
+
+// Robin static limit phi_g = gamma phi_i on one time level
+__global__ void k_robin_static(int prec, void* p, void* lo, Layout L, Faces F, const double* __restrict__ coef) {
+    long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= F.off[6]) return;
+    int gc[3], ic[3];
+    face_cell(F, L.nx, L.ny, L.nz, t, gc, ic);
+    const long long qg = L.at(gc[0], gc[1], gc[2]), qi = L.at(ic[0], ic[1], ic[2]);
+    write_phi(prec, p, lo, qg, __dmul_rn(coef[3 * t + 2], read_phi(prec, p, lo, qi)));
+}
+
+// periodic copy into the face ghosts of one time level
+__global__ void k_periodic(int prec, void* p, void* lo, Layout L, Faces F) {
+    long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= F.off[6]) return;
+    int gc[3], ic[3];
+    int f = face_cell(F, L.nx, L.ny, L.nz, t, gc, ic);
+    int src[3] = {gc[0], gc[1], gc[2]};
+    int n[3] = {L.nx, L.ny, L.nz};
+    src[f / 2] = (f % 2) ? 0 : n[f / 2] - 1;
+    const long long qg = L.at(gc[0], gc[1], gc[2]), qs = L.at(src[0], src[1], src[2]);
+    if (prec == HG_PREC_F64) {
+        ((double*)p)[qg] = ((const double*)p)[qs];
+    } else {
+        ((float*)p)[qg] = ((const float*)p)[qs];
+        ((float*)lo)[qg] = ((const float*)lo)[qs];
+    }
+}
+
+template <int LMAX>
+int run_moments(hg_grid* g, const void* rho, int dtype) {
+    constexpr int NQ = (LMAX + 1) * (LMAX + 1);
+    k_moments<LMAX><<<kRedBlocks, kRedThreads, 0, g->stream>>>(rho, dtype, g->nx, g->ny, g->nz, g->h, g->origin[0],
+                                                                g->origin[1], g->origin[2], g->ylm, g->red);
+    HG_LAUNCHED("multipole moment kernel");
+    k_finish<<<1, kRedThreads, 0, g->stream>>>(g->red, kRedBlocks, NQ, g->dres);
+    HG_LAUNCHED("moment finish kernel");
+    return HG_OK;
+}
+
+template <int LMAX>
+int run_dirichlet(hg_grid* g) {
+    QArr Q;
+    for (int q = 0; q < kMaxQ; ++q) Q.q[q] = q < (LMAX + 1) * (LMAX + 1) ? g->Q[q] : 0.0;
+    long long n = g->F.off[6];
+    int threads = 128;
+    k_dirichlet<LMAX><<<(unsigned)((n + threads - 1) / threads), threads, 0, g->stream>>>(
+        g->prec, g->phi[0], g->phi[1], g->lo[0], g->lo[1], g->L, g->F, g->h, g->origin[0], g->origin[1],
+        g->origin[2], g->G, Q, g->ylm);
+    HG_LAUNCHED("Dirichlet ghost kernel");
+    return HG_OK;
+}
+
+}  // namespace
+
+long long reduction_scratch_elems() { return (long long)kRedBlocks * kMaxQ; }
+
+int compute_moments(hg_grid* g, const void* rho_dense, int dtype) {
+    int rc;
+    switch (g->lmax) {
+        case 0: rc = run_moments<0>(g, rho_dense, dtype); break;
+        case 1: rc = run_moments<1>(g, rho_dense, dtype); break;
+        case 2: rc = run_moments<2>(g, rho_dense, dtype); break;
+        case 3: rc = run_moments<3>(g, rho_dense, dtype); break;
+        case 4: rc = run_moments<4>(g, rho_dense, dtype); break;
+        case 5: rc = run_moments<5>(g, rho_dense, dtype); break;
+        case 6: rc = run_moments<6>(g, rho_dense, dtype); break;
+        case 7: rc = run_moments<7>(g, rho_dense, dtype); break;
+        default: rc = run_moments<8>(g, rho_dense, dtype); break;
+    }
+    if (rc != HG_OK) return rc;
+    int nq = (g->lmax + 1) * (g->lmax + 1);
+    HG_CUDA(cudaMemcpyAsync(g->Q, g->dres, nq * sizeof(double), cudaMemcpyDeviceToHost, g->stream));
+    HG_CUDA(cudaStreamSynchronize(g->stream));
+    for (int q = nq; q < kMaxQ; ++q) g->Q[q] = 0.0;
+    g->have_Q = 1;
+    return HG_OK;
+}
+
+int set_ghosts_dirichlet(hg_grid* g) {
+    switch (g->lmax) {
+        case 0: return run_dirichlet<0>(g);
+        case 1: return run_dirichlet<1>(g);
+        case 2: return run_dirichlet<2>(g);
+        case 3: return run_dirichlet<3>(g);
+        case 4: return run_dirichlet<4>(g);
+        case 5: return run_dirichlet<5>(g);
+        case 6: return run_dirichlet<6>(g);
+        case 7: return run_dirichlet<7>(g);
+        default: return run_dirichlet<8>(g);
+    }
+}
+
+// periodic copies into the face ghosts of the level just written by a single sweep (buffer 1 - cur)
+int launch_periodic_copy(hg_grid* g) {
+    long long n = g->F.off[6];
+    int threads = 256;
+    unsigned blocks = (unsigned)((n + threads - 1) / threads);
+    int nxt = 1 - g->cur;
+    k_periodic<<<blocks, threads, 0, g->stream>>>(g->prec, g->phi[nxt], g->lo[nxt], g->L, g->F);
+    HG_LAUNCHED("periodic ghost kernel");
+    return HG_OK;
+}
+
+// ghosts of a freshly seeded state (both time levels)
+int seed_ghosts(hg_grid* g) {
+    long long n = g->F.off[6];
+    int threads = 256;
+    unsigned blocks = (unsigned)((n + threads - 1) / threads);
+    for (int b = 0; b < 2; ++b) {
+        if (g->bc == HG_BC_ROBIN) {
+            k_robin_static<<<blocks, threads, 0, g->stream>>>(g->prec, g->phi[b], g->lo[b], g->L, g->F, g->robin);
+            HG_LAUNCHED("Robin static ghost kernel");
+        } else if (g->bc == HG_BC_PERIODIC) {
+            k_periodic<<<blocks, threads, 0, g->stream>>>(g->prec, g->phi[b], g->lo[b], g->L, g->F);
+            HG_LAUNCHED("periodic ghost kernel");
+        }
+    }
+    if (g->bc == HG_BC_DIRICHLET_ANALYTIC || g->bc == HG_BC_DIRICHLET_MULTIPOLE) {
+        if (g->have_Q) return set_ghosts_dirichlet(g);
+    }
+    return HG_OK;
+}
+
+}  // namespace hg

@@ -1,0 +1,80 @@
+// Per-cell arithmetic of one sub-step, shared by the single-sweep and the temporally blocked kernels so that both
+// round identically (every operation is an explicit round-to-nearest intrinsic: no contraction choices are left
+// to the compiler).  arXiv 1602.05700, Sec. 1 Eq. HNeq., discretised as
+//   phi^{n+1} = 2 phi^n - phi^{n-1} + nu^2 sum_{6 nb}(phi^n_nb - phi^n) - s,  s = (c_h dt)^2 4 pi G (rho - rho_bar),
+// where s is the stored source (scaled once, in FP64, when the density is set).
+// The Laplacian is always summed as differences phi_nb - phi (exact for neighbouring values of similar size), never
+// as sum(phi_nb) - 6 phi: the latter carries an error of order eps |phi| per sub-step, which the lossless scheme
+// accumulates in its slow modes (about 3e-12 relative after 2000 sub-steps at 64^3 against ~3e-14).
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace hg {
+
+// f32 with compensated increments: phi^n = hi + lo, d = phi^n - phi^{n-1}.
+//   L  = sum(hi_nb - hi) + sum(lo_nb) - 6 lo          (neighbour order -x, +x, -y, +y, -z, +z)
+//   d' = d + (nu^2 L - s)
+//   (hi', lo') = Fast2Sum(hi, lo + d')
+__device__ __forceinline__ void f32k_update(float xl, float xr, float ys, float yn, float zm, float zp, float c,
+                                            float lxl, float lxr, float lys, float lyn, float lzm, float lzp, float lc,
+                                            float d, float s, float nu2, float& hi_o, float& lo_o, float& d_o) {
+    float Lh = __fadd_rn(__fsub_rn(xl, c), __fsub_rn(xr, c));
+    Lh = __fadd_rn(Lh, __fsub_rn(ys, c));
+    Lh = __fadd_rn(Lh, __fsub_rn(yn, c));
+    Lh = __fadd_rn(Lh, __fsub_rn(zm, c));
+    Lh = __fadd_rn(Lh, __fsub_rn(zp, c));
+    float Ll = __fadd_rn(__fadd_rn(__fadd_rn(lxl, lxr), __fadd_rn(lys, lyn)), __fadd_rn(lzm, lzp));
+    Ll = __fmaf_rn(-6.0f, lc, Ll);
+    const float inc = __fmaf_rn(nu2, __fadd_rn(Lh, Ll), -s);
+    const float dn = __fadd_rn(d, inc);
+    const float y = __fadd_rn(dn, lc);
+    const float t = __fadd_rn(c, y);
+    lo_o = __fsub_rn(y, __fsub_rn(t, c));
+    hi_o = t;
+    d_o = dn;
+}
+
+// f64: phi^{n+1} = c + ((c - prev) + fma(nu2, L, -s)), L = ((xl-c) + (xr-c)) + ((ys-c) + (yn-c)) + ((zm-c) + (zp-c)):
+// 15 FP64 instructions per cell
+__device__ __forceinline__ double f64_update(double xl, double xr, double ys, double yn, double zm, double zp, double c,
+                                             double prev, double s, double nu2) {
+    const double Lx = __dadd_rn(__dsub_rn(xl, c), __dsub_rn(xr, c));
+    const double Ly = __dadd_rn(__dsub_rn(ys, c), __dsub_rn(yn, c));
+    const double Lz = __dadd_rn(__dsub_rn(zm, c), __dsub_rn(zp, c));
+    const double L = __dadd_rn(__dadd_rn(Lx, Ly), Lz);
+    return __dadd_rn(c, __dadd_rn(__dsub_rn(c, prev), __fma_rn(nu2, L, -s)));
+}
+
+// Robin ghost sub-step (monopole radiation condition, upwinded): phi_g' = alpha phi_g + beta phi_i, in FP64
+__device__ __forceinline__ double robin_update(double alpha, double beta, double phi_g, double phi_i) {
+    return __fma_rn(alpha, phi_g, __dmul_rn(beta, phi_i));
+}
+
+// The same update for the compensated float state, without FP64 (GB300's FP64 and its f32<->f64 conversions are
+// slow): alpha, beta rounded to float; both products and their sum carried as float pairs by error-free
+// transformations (TwoProduct with an FMA, TwoSum), the compensations added, then one Fast2Sum.
+__device__ __forceinline__ void robin_update_f32k(float a, float b, float hg, float lg, float hin, float lin,
+                                                  float& hi_o, float& lo_o) {
+    const float p1 = __fmul_rn(a, hg);
+    const float e1 = __fmaf_rn(a, hg, -p1);
+    const float p2 = __fmul_rn(b, hin);
+    const float e2 = __fmaf_rn(b, hin, -p2);
+    const float s = __fadd_rn(p1, p2);
+    const float bv = __fsub_rn(s, p1);
+    const float e3 = __fadd_rn(__fsub_rn(p1, __fsub_rn(s, bv)), __fsub_rn(p2, bv));
+    float t = __fadd_rn(__fadd_rn(e1, e2), e3);
+    t = __fmaf_rn(a, lg, t);
+    t = __fmaf_rn(b, lin, t);
+    hi_o = __fadd_rn(s, t);
+    lo_o = __fsub_rn(t, __fsub_rn(hi_o, s));
+}
+
+// a double as a float and its rounding remainder
+__device__ __forceinline__ void split_f32(double v, float& hi, float& lo) {
+    hi = __double2float_rn(v);
+    lo = __double2float_rn(__dsub_rn(v, (double)hi));
+}
+__device__ __forceinline__ double join_f32(float hi, float lo) { return __dadd_rn((double)hi, (double)lo); }
+
+}  // namespace hg

@@ -1,0 +1,515 @@
+// C ABI of the hyperbolic self-gravity library (declarations and contracts in include/hg.h).
+// Host-side runtime: argument checks, device buffers, the sub-step loop and state movement.  Every arithmetic
+// step of the method runs in the kernels of stencil.cu, temporal.cu, boundary.cu and fields.cu.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <string>
+#include <vector>
+
+#include "hg_internal.cuh"
+
+namespace hg {
+
+static thread_local std::string g_last_error;
+
+int fail(int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+    return fail(HG_ERR_CUDA, "%s: %s (%s)", what, cudaGetErrorString(e), cudaGetErrorName(e));
+}
+
+int ensure_staging(hg_grid* g) {
+    if (g->staging) return HG_OK;
+    long long n = (long long)g->nx * g->ny * g->nz;
+    long long ng = (long long)(g->nx + 2) * (g->ny + 2) * (g->nz + 2);
+    long long want = 2 * n > ng ? 2 * n : ng;
+    HG_CUDA(cudaMalloc(&g->staging, (size_t)want * sizeof(double)));
+    return HG_OK;
+}
+
+static void fill_ylm_norms(YlmNorm& N) {
+    const double pi = 3.14159265358979323846;
+    for (int q = 0; q < kMaxQ; ++q) {
+        N.n[q] = 0.0;
+        N.inv_lm[q] = 0.0;
+    }
+    for (int l = 0; l <= kMaxL; ++l)
+        for (int m = 0; m <= l; ++m) {
+            double ratio = 1.0;  // (l-m)!/(l+m)!
+            for (int t = l - m + 1; t <= l + m; ++t) ratio /= (double)t;
+            double K = sqrt((2.0 * l + 1.0) / (4.0 * pi) * ratio);
+            N.n[l * l + l + m] = m == 0 ? K : sqrt(2.0) * K;
+            if (l > m) N.inv_lm[l * l + l + m] = 1.0 / (double)(l - m);
+        }
+}
+
+static int dt_size(int dtype) { return dtype == HG_DT_F64 ? 8 : 4; }
+
+// Robin coefficients (alpha, beta, gamma) of every face ghost; rejects nu/mu > 1 (unstable upwind update)
+static int build_robin(hg_grid* g) {
+    long long n = g->F.off[6];
+    std::vector<double> c((size_t)(3 * n));
+    double worst = 0.0;
+    for (long long t = 0; t < n; ++t) {
+        int gc[3], ic[3];
+        int f = face_cell(g->F, g->nx, g->ny, g->nz, t, gc, ic);
+        double xg[3], xi[3];
+        for (int a = 0; a < 3; ++a) {
+            xg[a] = g->origin[a] + (gc[a] + 0.5) * g->h;
+            xi[a] = g->origin[a] + (ic[a] + 0.5) * g->h;
+        }
+        double rg = sqrt(xg[0] * xg[0] + xg[1] * xg[1] + xg[2] * xg[2]);
+        double ri = sqrt(xi[0] * xi[0] + xi[1] * xi[1] + xi[2] * xi[2]);
+        double along = xg[f / 2] * ((f % 2) ? 1.0 : -1.0);  // x_g . n (outward normal)
+        if (!(rg > 0.0) || !(along > 0.0))
+            return fail(HG_ERR_CFL, "Robin boundary: ghost (%d,%d,%d) does not face away from the origin; the domain must "
+                                    "surround the coordinate origin", gc[0], gc[1], gc[2]);
+        double a = g->nu / (along / rg);
+        if (a > worst) worst = a;
+        c[3 * t] = 1.0 - a;
+        c[3 * t + 1] = a * ri / rg;
+        c[3 * t + 2] = ri / rg;
+    }
+    if (worst > 1.0 + 1e-12)
+        return fail(HG_ERR_CFL, "Robin boundary: nu/mu = %.6f > 1 at some ghost (reduce dt or centre the domain)", worst);
+    HG_CUDA(cudaMalloc(&g->robin, c.size() * sizeof(double)));
+    HG_CUDA(cudaMemcpy(g->robin, c.data(), c.size() * sizeof(double), cudaMemcpyHostToDevice));
+    std::vector<float2> c32((size_t)n);
+    for (long long t = 0; t < n; ++t) c32[t] = make_float2((float)c[3 * t], (float)c[3 * t + 1]);
+    HG_CUDA(cudaMalloc(&g->robin32, c32.size() * sizeof(float2)));
+    HG_CUDA(cudaMemcpy(g->robin32, c32.data(), c32.size() * sizeof(float2), cudaMemcpyHostToDevice));
+    return HG_OK;
+}
+
+static void release(hg_grid* g) {
+    void* ptrs[] = {g->phi[0], g->phi[1], g->lo[0], g->lo[1], g->dlt[0], g->dlt[1], g->rho, g->robin, g->robin32,
+                    g->red, g->dres, g->staging};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    if (g->prof_ev) {
+        for (int e = 0; e < 2 * kProfPairs; ++e) cudaEventDestroy(g->prof_ev[e]);
+        delete[] g->prof_ev;
+    }
+}
+
+int prof_fold(hg_grid* g) {
+    if (!g->prof_used) return HG_OK;
+    HG_CUDA(cudaStreamSynchronize(g->stream));
+    for (int p = 0; p < g->prof_used; ++p) {
+        float ms = 0.f;
+        HG_CUDA(cudaEventElapsedTime(&ms, g->prof_ev[2 * p], g->prof_ev[2 * p + 1]));
+        g->prof_ms += ms;
+    }
+    g->prof_count += g->prof_used;
+    g->prof_used = 0;
+    return HG_OK;
+}
+
+int prof_begin(hg_grid* g) {
+    if (!g->prof) return HG_OK;
+    if (g->prof_used == kProfPairs) {
+        int rc = prof_fold(g);
+        if (rc) return rc;
+    }
+    HG_CUDA(cudaEventRecord(g->prof_ev[2 * g->prof_used], g->stream));
+    return HG_OK;
+}
+
+int prof_end(hg_grid* g) {
+    if (!g->prof) return HG_OK;
+    HG_CUDA(cudaEventRecord(g->prof_ev[2 * g->prof_used + 1], g->stream));
+    ++g->prof_used;
+    return HG_OK;
+}
+
+static int check_grid(const hg_grid* g) {
+    if (!g) return fail(HG_ERR_ARG, "null grid");
+    cudaError_t e = cudaSetDevice(g->device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+    return HG_OK;
+}
+
+}  // namespace hg
+
+using namespace hg;
+
+extern "C" {
+
+const char* hg_last_error(void) { return g_last_error.c_str(); }
+
+int hg_init_grid(hg_grid** out, int nx, int ny, int nz, double h, const double origin[3], double c_h, double G,
+                 double dt, int precision, int bc, int lmax, void* cuda_stream) {
+    g_last_error.clear();
+    if (!out) return fail(HG_ERR_ARG, "null output pointer");
+    *out = nullptr;
+    if (nx < 1 || ny < 1 || nz < 1) return fail(HG_ERR_ARG, "grid sizes must be >= 1 (got %d %d %d)", nx, ny, nz);
+    if ((long long)nx * ny * nz > (1LL << 34)) return fail(HG_ERR_ARG, "grid too large");
+    if (!(h > 0.0) || !(c_h > 0.0) || !(dt > 0.0) || !isfinite(G) || !isfinite(h) || !isfinite(c_h) || !isfinite(dt))
+        return fail(HG_ERR_ARG, "h, c_h and dt must be positive and finite, G finite");
+    if (!origin || !isfinite(origin[0]) || !isfinite(origin[1]) || !isfinite(origin[2]))
+        return fail(HG_ERR_ARG, "origin must be 3 finite values");
+    if (precision != HG_PREC_F32K && precision != HG_PREC_F64) return fail(HG_ERR_ARG, "unknown precision %d", precision);
+    if (bc < HG_BC_DIRICHLET_ANALYTIC || bc > HG_BC_PERIODIC) return fail(HG_ERR_ARG, "unknown boundary condition %d", bc);
+    if (bc == HG_BC_DIRICHLET_MULTIPOLE && (lmax < 0 || lmax > HG_MAX_LMAX))
+        return fail(HG_ERR_ARG, "lmax must be in 0..%d", HG_MAX_LMAX);
+    double nu = c_h * dt / h;
+    if (nu * sqrt(3.0) > 1.0 + 1e-12)
+        return fail(HG_ERR_CFL, "nu sqrt(3) = %.6f > 1: the explicit scheme is unstable", nu * sqrt(3.0));
+
+    hg_grid* g = new hg_grid;
+    memset(g, 0, sizeof *g);
+    g->nx = nx;
+    g->ny = ny;
+    g->nz = nz;
+    g->h = h;
+    for (int a = 0; a < 3; ++a) g->origin[a] = origin[a];
+    g->c = c_h;
+    g->G = G;
+    g->dt = dt;
+    g->prec = precision;
+    g->bc = bc;
+    g->lmax = bc == HG_BC_DIRICHLET_MULTIPOLE ? lmax : 0;
+    g->stream = (cudaStream_t)cuda_stream;
+    g->nu = nu;
+    g->nu2 = nu * nu;
+    g->src = (c_h * dt) * (c_h * dt) * 4.0 * 3.14159265358979323846 * G;
+    g->esize = precision == HG_PREC_F64 ? 8 : 4;
+    g->L = make_layout(nx, ny, nz, g->esize);
+    g->F = make_faces(nx, ny, nz);
+    g->tdepth = 1;
+    fill_ylm_norms(g->ylm);
+    int rc = HG_OK;
+    cudaError_t e = cudaGetDevice(&g->device);
+    if (e != cudaSuccess) {
+        rc = cuda_fail(e, "cudaGetDevice");
+    }
+    if (rc == HG_OK && (bc == HG_BC_DIRICHLET_ANALYTIC || bc == HG_BC_DIRICHLET_MULTIPOLE)) {
+        for (long long t = 0; t < g->F.off[6] && rc == HG_OK; ++t) {
+            int gc[3], ic[3];
+            face_cell(g->F, nx, ny, nz, t, gc, ic);
+            double r2 = 0.0;
+            for (int a = 0; a < 3; ++a) {
+                double x = origin[a] + (gc[a] + 0.5) * h;
+                r2 += x * x;
+            }
+            if (!(r2 > 0.0)) rc = fail(HG_ERR_ARG, "a ghost cell centre sits at the expansion origin");
+        }
+    }
+    if (rc == HG_OK && bc == HG_BC_ROBIN) rc = build_robin(g);
+    size_t bytes = (size_t)g->L.elems * g->esize;
+    auto alloc = [&](void** p) {
+        if (rc != HG_OK) return;
+        cudaError_t e2 = cudaMalloc(p, bytes);
+        if (e2 != cudaSuccess) {
+            rc = cuda_fail(e2, "cudaMalloc(state)");
+            return;
+        }
+        e2 = cudaMemsetAsync(*p, 0, bytes, g->stream);
+        if (e2 != cudaSuccess) rc = cuda_fail(e2, "cudaMemsetAsync(state)");
+    };
+    alloc(&g->phi[0]);
+    alloc(&g->phi[1]);
+    alloc(&g->rho);
+    if (precision == HG_PREC_F32K) {
+        alloc(&g->lo[0]);
+        alloc(&g->lo[1]);
+        alloc(&g->dlt[0]);
+    }
+    if (rc == HG_OK) {
+        g->red_elems = reduction_scratch_elems();
+        e = cudaMalloc(&g->red, (size_t)g->red_elems * sizeof(double));
+        if (e == cudaSuccess) e = cudaMalloc(&g->dres, kMaxQ * sizeof(double));
+        if (e != cudaSuccess) rc = cuda_fail(e, "cudaMalloc(reduction scratch)");
+    }
+    if (rc == HG_OK) {
+        e = cudaStreamSynchronize(g->stream);
+        if (e != cudaSuccess) rc = cuda_fail(e, "cudaStreamSynchronize");
+    }
+    if (rc != HG_OK) {
+        release(g);
+        delete g;
+        return rc;
+    }
+    *out = g;
+    return HG_OK;
+}
+
+int hg_set_density(hg_grid* g, const void* rho, int dtype, int on_device) {
+    int rc = check_grid(g);
+    if (rc) return rc;
+    if (!rho) return fail(HG_ERR_ARG, "null density");
+    if (dtype != HG_DT_F32 && dtype != HG_DT_F64) return fail(HG_ERR_ARG, "unknown dtype %d", dtype);
+    const long long n = (long long)g->nx * g->ny * g->nz;
+    const void* src = rho;
+    if (!on_device) {
+        if ((rc = ensure_staging(g))) return rc;
+        HG_CUDA(cudaMemcpyAsync(g->staging, rho, (size_t)n * dt_size(dtype), cudaMemcpyHostToDevice, g->stream));
+        src = g->staging;
+    }
+    double sum = 0.0;
+    if ((rc = prepare_source(g, src, dtype, &sum))) return rc;
+    g->mass = sum * g->h * g->h * g->h;
+    g->rho_bar = g->bc == HG_BC_PERIODIC ? sum / (double)n : 0.0;
+    if (g->bc == HG_BC_DIRICHLET_ANALYTIC || g->bc == HG_BC_DIRICHLET_MULTIPOLE) {
+        if ((rc = compute_moments(g, src, dtype))) return rc;
+        if ((rc = set_ghosts_dirichlet(g))) return rc;
+    }
+    if (!on_device) HG_CUDA(cudaStreamSynchronize(g->stream));  // the staging buffer is reused by later calls
+    return HG_OK;
+}
+
+int hg_set_phi(hg_grid* g, const void* phi, const void* phi_prev, int dtype, int on_device) {
+    int rc = check_grid(g);
+    if (rc) return rc;
+    if (!phi) return fail(HG_ERR_ARG, "null phi");
+    if (dtype != HG_DT_F32 && dtype != HG_DT_F64) return fail(HG_ERR_ARG, "unknown dtype %d", dtype);
+    const long long n = (long long)g->nx * g->ny * g->nz;
+    const void* a = phi;
+    const void* b = phi_prev;
+    if (!on_device) {
+        if ((rc = ensure_staging(g))) return rc;
+        size_t bytes = (size_t)n * dt_size(dtype);
+        HG_CUDA(cudaMemcpyAsync(g->staging, phi, bytes, cudaMemcpyHostToDevice, g->stream));
+        a = g->staging;
+        if (phi_prev) {
+            HG_CUDA(cudaMemcpyAsync((char*)g->staging + bytes, phi_prev, bytes, cudaMemcpyHostToDevice, g->stream));
+            b = (const char*)g->staging + bytes;
+        }
+    }
+    if ((rc = set_phi_device(g, a, b, dtype))) return rc;
+    if ((rc = seed_ghosts(g))) return rc;
+    g->step = 0;
+    if (!on_device) HG_CUDA(cudaStreamSynchronize(g->stream));
+    return HG_OK;
+}
+
+int hg_set_temporal_depth(hg_grid* g, int k) {
+    int rc = check_grid(g);
+    if (rc) return rc;
+    if (k < 1 || k > HG_MAX_TEMPORAL_DEPTH)
+        return fail(HG_ERR_ARG, "temporal depth must be in 1..%d", HG_MAX_TEMPORAL_DEPTH);
+    if (k > 1 && g->prec != HG_PREC_F32K)
+        return fail(HG_ERR_ARG, "temporal blocking is built for HG_PREC_F32K only (FP64 sub-steps are bound by the "
+                                "FP64 pipe, not by HBM traffic, so fusing them saves nothing)");
+    if (k > 1 && !g->dlt[1]) {
+        size_t bytes = (size_t)g->L.elems * g->esize;
+        HG_CUDA(cudaMalloc(&g->dlt[1], bytes));
+        HG_CUDA(cudaMemsetAsync(g->dlt[1], 0, bytes, g->stream));
+    }
+    g->tdepth = k;
+    return HG_OK;
+}
+
+int hg_step(hg_grid* g, int n_substeps) {
+    int rc = check_grid(g);
+    if (rc) return rc;
+    if (n_substeps < 0) return fail(HG_ERR_ARG, "n_substeps must be >= 0");
+    int s = 0;
+    while (s < n_substeps) {
+        int k = n_substeps - s < g->tdepth ? n_substeps - s : g->tdepth;
+        // the sweep launches also write the Robin ghosts of the new level; the fused kernel the periodic ones too
+        if (k >= 2) {
+            if ((rc = launch_temporal(g, k))) return rc;
+        } else {
+            if ((rc = launch_step_single(g))) return rc;
+            if (g->bc == HG_BC_PERIODIC && (rc = launch_periodic_copy(g))) return rc;
+        }
+        g->cur = 1 - g->cur;
+        if (k >= 2) g->dcur = 1 - g->dcur;
+        s += k;
+        g->step += k;
+    }
+    return HG_OK;
+}
+
+int hg_accel(hg_grid* g, void* ax, void* ay, void* az, int dtype) {
+    int rc = check_grid(g);
+    if (rc) return rc;
+    if (!ax || !ay || !az) return fail(HG_ERR_ARG, "null acceleration buffer");
+    if (dtype != HG_DT_F32 && dtype != HG_DT_F64) return fail(HG_ERR_ARG, "unknown dtype %d", dtype);
+    return accel(g, ax, ay, az, dtype);
+}
+
+int hg_get_phi(hg_grid* g, void* out, int dtype, int on_device) {
+    int rc = check_grid(g);
+    if (rc) return rc;
+    if (!out) return fail(HG_ERR_ARG, "null output");
+    if (dtype != HG_DT_F32 && dtype != HG_DT_F64) return fail(HG_ERR_ARG, "unknown dtype %d", dtype);
+    if (on_device) return unpack_phi(g, out, dtype);
+    if ((rc = ensure_staging(g))) return rc;
+    if ((rc = unpack_phi(g, g->staging, dtype))) return rc;
+    size_t bytes = (size_t)g->nx * g->ny * g->nz * dt_size(dtype);
+    HG_CUDA(cudaMemcpyAsync(out, g->staging, bytes, cudaMemcpyDeviceToHost, g->stream));
+    HG_CUDA(cudaStreamSynchronize(g->stream));
+    return HG_OK;
+}
+
+int hg_get_phi_ghosted(hg_grid* g, double* out) {
+    int rc = check_grid(g);
+    if (rc) return rc;
+    if (!out) return fail(HG_ERR_ARG, "null output");
+    if ((rc = ensure_staging(g))) return rc;
+    if ((rc = unpack_phi_ghosted(g, g->staging))) return rc;
+    size_t bytes = (size_t)(g->nx + 2) * (g->ny + 2) * (g->nz + 2) * sizeof(double);
+    HG_CUDA(cudaMemcpyAsync(out, g->staging, bytes, cudaMemcpyDeviceToHost, g->stream));
+    HG_CUDA(cudaStreamSynchronize(g->stream));
+    return HG_OK;
+}
+
+int hg_get_stats(hg_grid* g, hg_stats* s) {
+    int rc = check_grid(g);
+    if (rc) return rc;
+    if (!s) return fail(HG_ERR_ARG, "null stats");
+    if ((rc = stats(g, s))) return rc;
+    if (s->nonfinite) return fail(HG_ERR_NONFINITE, "non-finite values in the state after %lld sub-steps", s->step);
+    return HG_OK;
+}
+
+int hg_get_moments(hg_grid* g, double* Q) {
+    int rc = check_grid(g);
+    if (rc) return rc;
+    if (!Q) return fail(HG_ERR_ARG, "null output");
+    if (!(g->bc == HG_BC_DIRICHLET_ANALYTIC || g->bc == HG_BC_DIRICHLET_MULTIPOLE) || !g->have_Q)
+        return fail(HG_ERR_STATE, "moments exist only for the Dirichlet modes after hg_set_density");
+    int nq = (g->lmax + 1) * (g->lmax + 1);
+    for (int q = 0; q < nq; ++q) Q[q] = g->Q[q];
+    return HG_OK;
+}
+
+int hg_compare(hg_grid* g, const double* phi_P, int on_device, double out[3]) {
+    int rc = check_grid(g);
+    if (rc) return rc;
+    if (!phi_P || !out) return fail(HG_ERR_ARG, "null argument");
+    const double* P = phi_P;
+    if (!on_device) {
+        if ((rc = ensure_staging(g))) return rc;
+        HG_CUDA(cudaMemcpyAsync(g->staging, phi_P, (size_t)g->nx * g->ny * g->nz * sizeof(double),
+                                cudaMemcpyHostToDevice, g->stream));
+        P = g->staging;
+    }
+    return compare(g, P, out);
+}
+
+// ---- checkpoint / resume ----
+struct StateHeader {
+    char magic[8];
+    int nx, ny, nz, prec, bc, lmax, cur, have_Q;
+    long long step;
+    double mass, rho_bar;
+    double Q[kMaxQ];
+};
+
+static int n_buffers(const hg_grid* g) { return g->prec == HG_PREC_F64 ? 3 : 6; }
+static void** buffer(hg_grid* g, int b) {
+    void** all[6] = {&g->phi[0], &g->phi[1], &g->rho, &g->lo[0], &g->lo[1], &g->dlt[g->dcur]};
+    return all[b];
+}
+
+size_t hg_state_bytes(const hg_grid* g) {
+    if (!g) return 0;
+    return sizeof(StateHeader) + (size_t)n_buffers(g) * (size_t)g->L.elems * g->esize;
+}
+
+int hg_save_state(hg_grid* g, void* host_buf) {
+    int rc = check_grid(g);
+    if (rc) return rc;
+    if (!host_buf) return fail(HG_ERR_ARG, "null buffer");
+    StateHeader H;
+    memset(&H, 0, sizeof H);
+    memcpy(H.magic, "HGSTATE1", 8);
+    H.nx = g->nx;
+    H.ny = g->ny;
+    H.nz = g->nz;
+    H.prec = g->prec;
+    H.bc = g->bc;
+    H.lmax = g->lmax;
+    H.cur = g->cur;
+    H.have_Q = g->have_Q;
+    H.step = g->step;
+    H.mass = g->mass;
+    H.rho_bar = g->rho_bar;
+    memcpy(H.Q, g->Q, sizeof H.Q);
+    memcpy(host_buf, &H, sizeof H);
+    char* p = (char*)host_buf + sizeof H;
+    size_t bytes = (size_t)g->L.elems * g->esize;
+    for (int b = 0; b < n_buffers(g); ++b, p += bytes)
+        HG_CUDA(cudaMemcpyAsync(p, *buffer(g, b), bytes, cudaMemcpyDeviceToHost, g->stream));
+    HG_CUDA(cudaStreamSynchronize(g->stream));
+    return HG_OK;
+}
+
+int hg_load_state(hg_grid* g, const void* host_buf) {
+    int rc = check_grid(g);
+    if (rc) return rc;
+    if (!host_buf) return fail(HG_ERR_ARG, "null buffer");
+    StateHeader H;
+    memcpy(&H, host_buf, sizeof H);
+    if (memcmp(H.magic, "HGSTATE1", 8) != 0 || H.nx != g->nx || H.ny != g->ny || H.nz != g->nz || H.prec != g->prec ||
+        H.bc != g->bc || H.lmax != g->lmax)
+        return fail(HG_ERR_ARG, "state buffer does not match this grid");
+    const char* p = (const char*)host_buf + sizeof H;
+    size_t bytes = (size_t)g->L.elems * g->esize;
+    for (int b = 0; b < n_buffers(g); ++b, p += bytes)
+        HG_CUDA(cudaMemcpyAsync(*buffer(g, b), p, bytes, cudaMemcpyHostToDevice, g->stream));
+    HG_CUDA(cudaStreamSynchronize(g->stream));
+    g->cur = H.cur;
+    g->have_Q = H.have_Q;
+    g->step = H.step;
+    g->mass = H.mass;
+    g->rho_bar = H.rho_bar;
+    memcpy(g->Q, H.Q, sizeof H.Q);
+    return HG_OK;
+}
+
+int hg_profile(hg_grid* g, int enable) {
+    int rc = check_grid(g);
+    if (rc) return rc;
+    if (enable && !g->prof_ev) {
+        g->prof_ev = new cudaEvent_t[2 * kProfPairs];
+        for (int e = 0; e < 2 * kProfPairs; ++e) HG_CUDA(cudaEventCreate(&g->prof_ev[e]));
+    }
+    if (!enable && (rc = prof_fold(g))) return rc;
+    g->prof = enable ? 1 : 0;
+    return HG_OK;
+}
+
+int hg_profile_read(hg_grid* g, double* substep_kernel_ms, long long* substep_launches, long long* kernel_launches) {
+    int rc = check_grid(g);
+    if (rc) return rc;
+    if ((rc = prof_fold(g))) return rc;
+    if (substep_kernel_ms) *substep_kernel_ms = g->prof_ms;
+    if (substep_launches) *substep_launches = g->prof_count;
+    if (kernel_launches) *kernel_launches = g->launches;
+    g->prof_ms = 0.0;
+    g->prof_count = 0;
+    return HG_OK;
+}
+
+int hg_sync(hg_grid* g) {
+    int rc = check_grid(g);
+    if (rc) return rc;
+    HG_CUDA(cudaStreamSynchronize(g->stream));
+    HG_CUDA(cudaGetLastError());
+    return HG_OK;
+}
+
+void hg_free(hg_grid* g) {
+    if (!g) return;
+    cudaSetDevice(g->device);
+    cudaStreamSynchronize(g->stream);
+    release(g);
+    delete g;
+}
+
+}  // extern "C"

@@ -1,0 +1,217 @@
+// Internal definitions shared by the translation units of the CUDA library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "hg.h"
+
+namespace hg {
+
+// ---- device memory layout ------------------------------------------------------------------------------------
+// Every per-cell field of a grid lives in one "padded" array of pitch * (ny+2) * (nz+2) elements: z-planes of
+// (ny+2) rows of `pitch` elements.  Row index j+1 and plane index k+1 hold interior cell (i,j,k); the ghost rows
+// and planes are j = -1, ny and k = -1, nz.  Inside a row the interior starts at element `xoff` (16 bytes), so the
+// x ghosts sit at xoff-1 and xoff+nx and every 4-cell group starting at a multiple of 4 is one aligned 16-byte
+// (float4 / 2 x double2) access.  The pitch is a multiple of 128 bytes and leaves room for a full vector read of
+// the last group of a row.
+struct Layout {
+    int nx, ny, nz;
+    int xoff;      // elements before interior x = 0 in a row
+    long long pitch;  // elements per row
+    long long plane;  // elements per z-plane = pitch * (ny + 2)
+    long long elems;  // total elements = plane * (nz + 2)
+    __host__ __device__ long long at(int i, int j, int k) const {
+        return (long long)(k + 1) * plane + (long long)(j + 1) * pitch + xoff + i;
+    }
+};
+
+inline Layout make_layout(int nx, int ny, int nz, int esize) {
+    Layout L;
+    L.nx = nx;
+    L.ny = ny;
+    L.nz = nz;
+    L.xoff = 16 / esize;
+    int align = 128 / esize;
+    long long need = (long long)L.xoff + nx + 4;
+    L.pitch = (need + align - 1) / align * align;
+    L.plane = L.pitch * (ny + 2);
+    L.elems = L.plane * (nz + 2);
+    return L;
+}
+
+// ---- face ghosts -----------------------------------------------------------------------------------------------
+// Faces f = 0..5 are -x, +x, -y, +y, -z, +z.  Face f has na x nb ghost cells; x faces are indexed (a,b) = (j,k),
+// y faces (i,k), z faces (i,j).  Ghosts of all faces are enumerated face after face, a fastest.
+struct Faces {
+    long long off[7];
+    int na[6], nb[6];
+};
+
+inline Faces make_faces(int nx, int ny, int nz) {
+    Faces F;
+    int n[3] = {nx, ny, nz};
+    F.off[0] = 0;
+    for (int f = 0; f < 6; ++f) {
+        int axis = f / 2;
+        int t0 = axis == 0 ? 1 : 0, t1 = axis == 2 ? 1 : 2;
+        F.na[f] = n[t0];
+        F.nb[f] = n[t1];
+        F.off[f + 1] = F.off[f] + (long long)F.na[f] * F.nb[f];
+    }
+    return F;
+}
+
+// ghost cell (g) and interior neighbour (in) of face ghost number t; returns the face
+__host__ __device__ inline int face_cell(const Faces& F, int nx, int ny, int nz, long long t, int g[3], int in[3]) {
+    int f = 0;
+    while (f < 5 && t >= F.off[f + 1]) ++f;
+    long long r = t - F.off[f];
+    int a = (int)(r % F.na[f]), b = (int)(r / F.na[f]);
+    int axis = f / 2, hi = f % 2;
+    int n[3] = {nx, ny, nz};
+    int t0 = axis == 0 ? 1 : 0, t1 = axis == 2 ? 1 : 2;
+    g[t0] = a;
+    g[t1] = b;
+    g[axis] = hi ? n[axis] : -1;
+    in[0] = g[0];
+    in[1] = g[1];
+    in[2] = g[2];
+    in[axis] = hi ? n[axis] - 1 : 0;
+    return f;
+}
+
+// ---- multipole constants -----------------------------------------------------------------------------------------
+constexpr int kMaxL = HG_MAX_LMAX;
+constexpr int kMaxQ = (kMaxL + 1) * (kMaxL + 1);
+struct YlmNorm {
+    double n[kMaxQ];        // normalisation of r^l Y_lm written as n_lm * q_l^m(z, r^2) * {C_m, S_m}
+    double inv_lm[kMaxQ];   // 1 / (l - m) for the upward recurrence (index l*l + l + m, m >= 0)
+};
+
+// ---- the grid --------------------------------------------------------------------------------------------------
+}  // namespace hg
+
+struct hg_grid {
+    int nx, ny, nz;
+    double h;
+    double origin[3];
+    double c, G, dt;
+    int prec, bc, lmax;
+    cudaStream_t stream;
+    int device;
+    double nu, nu2, src;  // nu = c dt / h, nu^2, (c dt)^2 4 pi G
+    int esize;
+    hg::Layout L;
+    hg::Faces F;
+    // state: F64 -> phi[cur] = phi^n, phi[1-cur] = phi^{n-1};
+    //        F32K -> phi[cur] (the float part) + lo[cur] (its compensation) = phi^n, dlt[dcur] = phi^n - phi^{n-1}
+    //        (dlt[1] exists once temporal blocking is enabled: fused sub-steps read neighbours' dlt, so it ping-pongs)
+    void* phi[2];
+    void* lo[2];
+    void* dlt[2];
+    int dcur;
+    void* rho;  // stored source s = (c dt)^2 4 pi G (rho - rho_bar), rho_bar = mean(rho) for periodic boundaries, else 0
+    int cur;
+    double* robin;  // 3 doubles per face ghost: alpha, beta, gamma (see boundary.cu)
+    float2* robin32;  // alpha, beta rounded to float (compensated float grids)
+    double* red;    // reduction scratch
+    long long red_elems;
+    double* dres;   // small device result buffer
+    double* staging;  // dense nz*ny*nx doubles, allocated on first host transfer
+    double Q[hg::kMaxQ];
+    int have_Q;
+    double mass, rho_bar;
+    long long step;
+    int tdepth;
+    hg::YlmNorm ylm;
+    // measurement: kernel launch count and CUDA events around the sub-step kernel
+    long long launches;
+    int prof;
+    int prof_used;          // event pairs recorded since the last fold
+    double prof_ms;         // folded time
+    long long prof_count;   // folded launches
+    cudaEvent_t* prof_ev;   // 2 * kProfPairs events, created when profiling is first enabled
+};
+
+namespace hg {
+
+// error reporting (thread-local message)
+int fail(int code, const char* fmt, ...);
+int cuda_fail(cudaError_t e, const char* what);
+#define HG_CUDA(call)                                     \
+    do {                                                  \
+        cudaError_t e_ = (call);                          \
+        if (e_ != cudaSuccess) return hg::cuda_fail(e_, #call); \
+    } while (0)
+// after every kernel launch of a grid `g` in scope: count it and report a launch failure
+#define HG_LAUNCHED(what)                                 \
+    do {                                                  \
+        ++g->launches;                                    \
+        cudaError_t e_ = cudaGetLastError();              \
+        if (e_ != cudaSuccess) return hg::cuda_fail(e_, what); \
+    } while (0)
+
+// kernels' host launchers (each returns HG_OK or an error code)
+int launch_step_single(hg_grid* g);                  // one interior sweep: cur -> 1-cur (stencil.cu)
+int launch_periodic_copy(hg_grid* g);                // periodic ghosts of the new level after a single sweep
+int launch_temporal(hg_grid* g, int k);              // k fused sub-steps: cur -> 1-cur (temporal.cu)
+int ensure_staging(hg_grid* g);
+int prepare_source(hg_grid* g, const void* src, int dtype, double* sum_host);  // dense rho -> stored s
+int set_ghosts_dirichlet(hg_grid* g);                // multipole data into both buffers
+int compute_moments(hg_grid* g, const void* rho_dense, int dtype);
+int seed_ghosts(hg_grid* g);                         // after hg_set_phi
+int reduce_sum(hg_grid* g, const void* dense, int dtype, double* out_host);
+int stats(hg_grid* g, hg_stats* s);
+int compare(hg_grid* g, const double* phiP_dense, double out[3]);
+int accel(hg_grid* g, void* ax, void* ay, void* az, int dtype);
+int unpack_phi(hg_grid* g, void* dst_dense, int dtype);
+int unpack_phi_ghosted(hg_grid* g, double* dst);
+int set_phi_device(hg_grid* g, const void* phi_dense, const void* prev_dense, int dtype);
+constexpr int kProfPairs = 4096;
+int prof_begin(hg_grid* g);  // record the start event of a sub-step kernel launch (no-op unless profiling)
+int prof_end(hg_grid* g);
+int prof_fold(hg_grid* g);   // synchronise and add the recorded pairs to prof_ms
+
+// ---- deterministic reductions --------------------------------------------------------------------------------
+constexpr int kRedThreads = 256;
+constexpr int kRedBlocks = 304;  // 2 per SM; fixed so that the reduction order, hence the result, is reproducible
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+// block sum (or max) of one value per thread; blockDim.x a multiple of 32; result valid in thread 0
+__device__ __forceinline__ double block_reduce(double v, double* sh, bool is_max) {
+    v = is_max ? warp_max(v) : warp_sum(v);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) sh[w] = v;
+    __syncthreads();
+    double r = 0.0;
+    if (w == 0) {
+        r = l < (int)(blockDim.x >> 5) ? sh[l] : 0.0;
+        r = is_max ? warp_max(r) : warp_sum(r);
+    }
+    return r;
+}
+__device__ __forceinline__ double block_sum(double v, double* sh) { return block_reduce(v, sh, false); }
+
+long long reduction_scratch_elems();
+
+inline int grid_blocks(long long n, int threads, int cap) {
+    long long b = (n + threads - 1) / threads;
+    if (b > cap) b = cap;
+    if (b < 1) b = 1;
+    return (int)b;
+}
+
+}  // namespace hg

@@ -1,0 +1,241 @@
+// Temporal blocking: K consecutive sub-steps of the hyperbolic gravity equation per round trip through HBM
+// (arXiv 1602.05700, Sec. 2: rho is frozen during the wave sub-steps of a hydro step, so K sub-steps can be fused
+// without reading the source again).  FP32-compensated state only (hi + lo = phi^n, dlt = phi^n - phi^{n-1}).
+//
+// A block of 32 x 32 threads owns a 32 x 32 column region of the x-y plane and marches in z through a chunk of
+// output planes.  Level 0 (the state at sub-step n) is read once per plane; level t = 1..K is computed one plane
+// behind level t-1 (a z pipeline), each level keeping its last three planes (hi, lo) and last two dlt in registers.
+// The x/y neighbours of the plane being updated come from a shared-memory copy of level t-1's middle plane
+// (double-buffered so one barrier per level suffices).  Level t is valid on the region shrunk by t cells on each
+// side, so the 32 - 2K inner columns are written at level K: the K-cell halos are recomputed redundantly by the
+// neighbouring blocks instead of being exchanged.
+//
+// Boundary cells inside the region follow the boundary condition at every level: Dirichlet ghosts keep their
+// data, Robin ghosts take the radiation-condition update (the same float-pair formula as the single-sweep ghost
+// kernel),
+// periodic regions load wrapped coordinates and are all interior.  Output tiles cover x in [-1, nx], y in [-1, ny]
+// and z in [-1, nz], so the face ghosts of level n+K (Robin updates, periodic copies) are written too.  Every update uses the arithmetic of cell.cuh,
+// so K fused sub-steps give bit-for-bit the result of K single sweeps.
+//
+// HBM bytes per cell per K sub-steps: read hi, lo, dlt, rho + write hi, lo, dlt = 28 B (plus halo re-reads, which
+// the neighbouring blocks mostly find in L2), i.e. 28/K B per cell-update against 28 B for a single sweep.
+#include "cell.cuh"
+#include "hg_internal.cuh"
+
+namespace hg {
+
+namespace {
+
+constexpr int TB = 32;  // region side (threads per side)
+
+struct TParams {
+    const float* hi_c;
+    const float* lo_c;
+    const float* d_c;
+    const float* rho;  // scaled source s
+    float* hi_n;
+    float* lo_n;
+    float* d_n;
+    const float2* robin32;  // (alpha, beta) per face ghost rounded to float, Robin only
+    Layout L;
+    Faces F;
+    float nu2;
+    int bc;
+    int zchunk;
+};
+
+__device__ __forceinline__ int wrap(int v, int n) {
+    v %= n;
+    return v < 0 ? v + n : v;
+}
+
+template <int K>
+__global__ void __launch_bounds__(TB* TB, 1) k_temporal_f32k(const TParams P) {
+    constexpr int W = TB - 2 * K;  // output columns per side
+    __shared__ float2 sh[2][TB][TB];
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const Layout& L = P.L;
+    const bool periodic = P.bc == HG_BC_PERIODIC;
+    const bool robin = P.bc == HG_BC_ROBIN;
+    const int x = -1 + (int)blockIdx.x * W + tx - K;
+    const int y = -1 + (int)blockIdx.y * W + ty - K;
+    const int z0 = -1 + (int)blockIdx.z * P.zchunk;
+    const int z1 = min(L.nz + 1, z0 + P.zchunk);  // output planes [z0, z1)
+
+    // column classification (non-periodic): interior, x-face ghost, y-face ghost, or dead
+    const bool xin = x >= 0 && x < L.nx, yin = y >= 0 && y < L.ny;
+    const bool xg = x == -1 || x == L.nx, yg = y == -1 || y == L.ny;
+    const bool col_int = periodic || (xin && yin);
+    const bool col_fx = !periodic && xg && yin;
+    const bool col_fy = !periodic && xin && yg;
+    const bool loadable_col = periodic || (x >= -1 && x <= L.nx && y >= -1 && y <= L.ny);
+    const int xw = periodic ? wrap(x, L.nx) : x;
+    const int yw = periodic ? wrap(y, L.ny) : y;
+    const bool out_col = tx >= K && tx < TB - K && ty >= K && ty < TB - K && x >= -1 && x <= L.nx && y >= -1 &&
+                         y <= L.ny;
+
+    float qh[K][3], ql[K][3], dq[K][2], rq[K + 1];
+#pragma unroll
+    for (int t = 0; t < K; ++t) {
+        qh[t][0] = qh[t][1] = qh[t][2] = 0.f;
+        ql[t][0] = ql[t][1] = ql[t][2] = 0.f;
+        dq[t][0] = dq[t][1] = 0.f;
+    }
+#pragma unroll
+    for (int t = 0; t <= K; ++t) rq[t] = 0.f;
+
+    auto load = [&](int p, float& h, float& l, float& d, float& r) {
+        h = l = d = r = 0.f;
+        if (!loadable_col) return;
+        int pw = p;
+        if (periodic) {
+            pw = wrap(p, L.nz);
+        } else if (p < -1 || p > L.nz) {
+            return;
+        }
+        const long long q = L.at(xw, yw, pw);
+        h = __ldg(P.hi_c + q);
+        l = __ldg(P.lo_c + q);
+        d = __ldg(P.d_c + q);
+        r = __ldg(P.rho + q);
+    };
+
+    float nh, nl, nd, nr;
+    load(z0 - K, nh, nl, nd, nr);
+    int lvl = 0;
+    for (int p = z0 - K; p < z1 + K; ++p) {
+        // shift level 0 in (plane p), prefetch plane p + 1
+        const float h0 = nh, l0 = nl, d0 = nd, r0 = nr;
+        if (p + 1 < z1 + K) load(p + 1, nh, nl, nd, nr);
+        qh[0][0] = qh[0][1];
+        qh[0][1] = qh[0][2];
+        qh[0][2] = h0;
+        ql[0][0] = ql[0][1];
+        ql[0][1] = ql[0][2];
+        ql[0][2] = l0;
+        dq[0][0] = dq[0][1];
+        dq[0][1] = d0;
+#pragma unroll
+        for (int t = K; t > 0; --t) rq[t] = rq[t - 1];
+        rq[0] = r0;
+
+#pragma unroll
+        for (int t = 1; t <= K; ++t) {
+            const int pt = p - t;  // plane level t computes in this iteration
+            const float c = qh[t - 1][1], lc = ql[t - 1][1];
+            const float dprev = dq[t - 1][0];
+            const int b = lvl & 1;
+            ++lvl;
+            sh[b][ty][tx] = make_float2(c, lc);
+            __syncthreads();
+            float oh = c, ol = lc, od = dprev;
+            const bool in_win = tx >= t && tx < TB - t && ty >= t && ty < TB - t && pt >= z0 - (K - t) &&
+                                pt < z1 + (K - t);
+            if (in_win) {
+                const bool zin = periodic || (pt >= 0 && pt < L.nz);
+                const bool zg = !periodic && (pt == -1 || pt == L.nz);
+                if (col_int && zin) {
+                    const float2 xl = sh[b][ty][tx - 1], xr = sh[b][ty][tx + 1];
+                    const float2 ys = sh[b][ty - 1][tx], yn = sh[b][ty + 1][tx];
+                    f32k_update(xl.x, xr.x, ys.x, yn.x, qh[t - 1][0], qh[t - 1][2], c, xl.y, xr.y, ys.y, yn.y,
+                                ql[t - 1][0], ql[t - 1][2], lc, dprev, rq[t], P.nu2, oh, ol, od);
+                } else if (robin && ((col_int && zg) || ((col_fx || col_fy) && zin))) {
+                    // Robin face ghost: inward neighbour and coefficient row
+                    float2 in;
+                    long long row;
+                    if (col_fx) {
+                        in = x < 0 ? sh[b][ty][tx + 1] : sh[b][ty][tx - 1];
+                        row = P.F.off[x < 0 ? 0 : 1] + (long long)pt * L.ny + y;
+                    } else if (col_fy) {
+                        in = y < 0 ? sh[b][ty + 1][tx] : sh[b][ty - 1][tx];
+                        row = P.F.off[y < 0 ? 2 : 3] + (long long)pt * L.nx + x;
+                    } else {
+                        in = pt < 0 ? make_float2(qh[t - 1][2], ql[t - 1][2]) : make_float2(qh[t - 1][0], ql[t - 1][0]);
+                        row = P.F.off[pt < 0 ? 4 : 5] + (long long)y * L.nx + x;
+                    }
+                    const float2 ab = P.robin32[row];
+                    robin_update_f32k(ab.x, ab.y, c, lc, in.x, in.y, oh, ol);
+                }
+            }
+            if (t < K) {
+                qh[t][0] = qh[t][1];
+                qh[t][1] = qh[t][2];
+                qh[t][2] = oh;
+                ql[t][0] = ql[t][1];
+                ql[t][1] = ql[t][2];
+                ql[t][2] = ol;
+                dq[t][0] = dq[t][1];
+                dq[t][1] = od;
+            } else if (out_col && pt >= z0 && pt < z1) {
+                if (periodic) {
+                    // interior cells, and the face ghosts as copies of the wrapped cells (the same values the
+                    // blocks owning those cells compute, from the same inputs)
+                    const int nout = (x < 0 || x >= L.nx) + (y < 0 || y >= L.ny) + (pt < 0 || pt >= L.nz);
+                    if (nout <= 1 && pt >= -1 && pt <= L.nz) {
+                        const long long q = L.at(x, y, pt);
+                        P.hi_n[q] = oh;
+                        P.lo_n[q] = ol;
+                        if (nout == 0) P.d_n[q] = od;
+                    }
+                } else {
+                    const bool zin = pt >= 0 && pt < L.nz;
+                    const bool zg = pt == -1 || pt == L.nz;
+                    const long long q = L.at(x, y, pt);
+                    if (col_int && zin) {
+                        P.hi_n[q] = oh;
+                        P.lo_n[q] = ol;
+                        P.d_n[q] = od;
+                    } else if (robin && ((col_int && zg) || ((col_fx || col_fy) && zin))) {
+                        P.hi_n[q] = oh;
+                        P.lo_n[q] = ol;
+                    }
+                }
+            }
+        }
+    }
+}
+
+template <int K>
+int launch_k(hg_grid* g, const TParams& P, int zchunk) {
+    constexpr int W = TB - 2 * K;
+    dim3 block(TB, TB);
+    dim3 grid((g->nx + 2 + W - 1) / W, (g->ny + 2 + W - 1) / W, (g->nz + 2 + zchunk - 1) / zchunk);
+    k_temporal_f32k<K><<<grid, block, 0, g->stream>>>(P);
+    HG_LAUNCHED("temporal sub-step kernel");
+    return HG_OK;
+}
+
+}  // namespace
+
+int launch_temporal(hg_grid* g, int k) {
+    if (g->prec != HG_PREC_F32K || !g->dlt[1]) return fail(HG_ERR_STATE, "temporal blocking needs an f32k grid");
+    int nxt = 1 - g->cur;
+    TParams P;
+    P.hi_c = (const float*)g->phi[g->cur];
+    P.lo_c = (const float*)g->lo[g->cur];
+    P.d_c = (const float*)g->dlt[g->dcur];
+    P.rho = (const float*)g->rho;
+    P.hi_n = (float*)g->phi[nxt];
+    P.lo_n = (float*)g->lo[nxt];
+    P.d_n = (float*)g->dlt[1 - g->dcur];
+    P.robin32 = g->robin32;
+    P.L = g->L;
+    P.F = g->F;
+    P.nu2 = (float)g->nu2;
+    P.bc = g->bc;
+    int zchunk = 64;
+    if (zchunk > g->nz + 2) zchunk = g->nz + 2;
+    P.zchunk = zchunk;
+    int rc = prof_begin(g);
+    if (rc) return rc;
+    switch (k) {
+        case 2: rc = launch_k<2>(g, P, zchunk); break;
+        case 3: rc = launch_k<3>(g, P, zchunk); break;
+        case 4: rc = launch_k<4>(g, P, zchunk); break;
+        default: return fail(HG_ERR_ARG, "temporal depth %d not built", k);
+    }
+    if (rc) return rc;
+    return prof_end(g);
+}
+
+}  // namespace hg

@@ -117,3 +117,24 @@ def batch_sides(count: int, seed: int, choices=(64, 96, 128, 160, 192)) -> np.nd
 def batch_blob_counts(count: int, seed: int) -> np.ndarray:
     rng = np.random.Generator(np.random.PCG64(seed + 1000))
     return rng.integers(1, 7, size=count)
+
+
+def blob_density_torch(nx: int, blobs: np.ndarray, device, dtype, ny: int | None = None, nz: int | None = None,
+                       h: float | None = None, lo: float = -0.5):
+    """The same field as blob_density, evaluated with torch on a device (for large benchmark inputs)."""
+    import torch
+
+    ny = ny or nx
+    nz = nz or nx
+    h = 1.0 / nx if h is None else h
+    f64 = torch.float64
+    xs = lo + (torch.arange(nx, device=device, dtype=f64) + 0.5) * h
+    ys = lo + (torch.arange(ny, device=device, dtype=f64) + 0.5) * h
+    zs = lo + (torch.arange(nz, device=device, dtype=f64) + 0.5) * h
+    rho = torch.zeros((nz, ny, nx), device=device, dtype=dtype)
+    for cxb, cyb, czb, s, a in blobs:
+        ex = torch.exp(-((xs - cxb) ** 2) / (2 * s * s))
+        ey = torch.exp(-((ys - cyb) ** 2) / (2 * s * s))
+        ez = torch.exp(-((zs - czb) ** 2) / (2 * s * s))
+        rho += (a * ez[:, None, None] * ey[None, :, None] * ex[None, None, :]).to(dtype)
+    return rho
