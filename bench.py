@@ -348,6 +348,168 @@ def run_reference(args):
             "e2e": {"value": round(v, 5), "unit": "Gcell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+# ---- the other workloads (reported in the design doc; the default run above is the headline) --------------------------
+
+def run_precision(args):
+    """Config 2: 256^3 sphere + 8 blobs (seed 1), multipole boundary l <= 4, 2000 sub-steps in FP32-compensated and
+    FP64 on the GPU against the FP64 CPU oracle (which takes minutes on one core at this size)."""
+    import numpy as np
+    import torch
+
+    import oracle as O
+    import paper_1602_05700_gb300 as hg
+    from paper_1602_05700_gb300 import inputs as I
+
+    n, T = args.n, args.substeps
+    rho = I.sphere_density(n) + I.blob_density(n, I.draw_blobs(8, 1))
+    out = {"workload": f"{n}^3 sphere + 8 blobs, multipole Dirichlet l <= 4, {T} sub-steps, CFL 0.5", "results": {}}
+    phis = {}
+    for prec in ("f32k", "f64"):
+        g = hg.Grid.unit_cube(n, 1.0, 1.0, 0.5, prec, "multipole", lmax=4)
+        g.set_density(torch.from_numpy(rho).cuda())
+        g.step(3)
+        g.set_phi(torch.zeros((n, n, n), dtype=torch.float64, device="cuda"))
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        g.step(T)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        phis[prec] = g.phi(torch.float64, "cpu")
+        out["results"][prec] = {"gcell_updates_per_s": round(n ** 3 * T / (ms * 1e-3) / 1e9, 2), "ms": round(ms, 1)}
+        g.free()
+    og = O.unit_cube(n, 1.0, 1.0, 0.5, O.BC_DIRICHLET)
+    p, q = O.initial_state(og, rho, lmax=4)
+    t0 = time.perf_counter()
+    O.run(og, p, q, rho, T)
+    out["oracle_seconds"] = round(time.perf_counter() - t0, 1)
+    ref = p[1:-1, 1:-1, 1:-1]
+    for prec, phi in phis.items():
+        out["results"][prec]["rel_l2_vs_oracle"] = float(np.linalg.norm(phi - ref) / np.linalg.norm(ref))
+        out["results"][prec]["rel_linf_vs_oracle"] = float(np.abs(phi - ref).max() / np.abs(ref).max())
+    return out
+
+
+def run_batch(args):
+    """Config 4: 48 grids, sides uniform in {64, 96, 128, 160, 192} (seed 7), 1-6 blobs each, FP32-compensated for
+    even and FP64 for odd indices, Robin boundary, 500 sub-steps: one graph launch of batched sub-steps against
+    sequential per-grid launches (same work, same results)."""
+    import torch
+
+    import paper_1602_05700_gb300 as hg
+    from paper_1602_05700_gb300 import inputs as I
+
+    sides = I.batch_sides(48, 7)
+    nblobs = I.batch_blob_counts(48, 7)
+    T = args.substeps
+
+    def grids():
+        gs = []
+        for i, (n, nb) in enumerate(zip(sides, nblobs)):
+            n = int(n)
+            g = hg.Grid.unit_cube(n, 1.0, 1.0, 0.5, "f32k" if i % 2 == 0 else "f64", "robin")
+            g.set_density(I.blob_density_torch(n, I.draw_blobs(int(nb), 700 + i), "cuda", torch.float64))
+            gs.append(g)
+        return gs
+
+    cells = int(sum(int(n) ** 3 for n in sides))
+    res = {"workload": f"48 grids, sides {sorted(set(int(s) for s in sides))} (seed 7), mixed f32k/f64, Robin, "
+                       f"{T} sub-steps", "cells": cells}
+    gs = grids()
+    b = hg.Batch(gs)
+    b.step(8)  # autotune + graph for 8
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    b.step(T)
+    e1.record()
+    torch.cuda.synchronize()
+    ms_b = e0.elapsed_time(e1)
+    res["batched_graph"] = {"ms": round(ms_b, 2), "gcell_updates_per_s": round(cells * T / (ms_b * 1e-3) / 1e9, 2),
+                            **b.info()}
+    gs2 = grids()
+    for g in gs2:
+        g.step(2)
+    torch.cuda.synchronize()
+    e0.record()
+    for g in gs2:
+        g.step(T)
+    e1.record()
+    torch.cuda.synchronize()
+    ms_s = e0.elapsed_time(e1)
+    res["sequential_per_grid"] = {"ms": round(ms_s, 2), "gcell_updates_per_s": round(cells * T / (ms_s * 1e-3) / 1e9, 2)}
+    res["speedup"] = round(ms_s / ms_b, 3)
+    f32 = [i for i in range(48) if i % 2 == 0]
+    res["f32k_cells"] = int(sum(int(sides[i]) ** 3 for i in f32))
+    return res
+
+
+def run_adjoint(args):
+    """Config 5: 128^3, 4 blobs (seed 3), T = 400, 64 probes in |x| < 0.4 (seed 11), target from the seed-4 density,
+    L = sum (phi^T(x_p) - target)^2; dL/drho by the adjoint (no checkpoints, and checkpointed every K), checked against
+    central differences on 32 random cells; time and memory against storing the whole trajectory."""
+    import numpy as np
+    import torch
+
+    import paper_1602_05700_gb300 as hg
+    from paper_1602_05700_gb300 import autograd as HA
+    from paper_1602_05700_gb300 import inputs as I
+
+    n, T = args.n, args.substeps
+    out = {"workload": f"{n}^3, 4 blobs seed 3, T = {T}, 64 probes", "results": {}}
+    for prec in ("f64", "f32k"):
+        grid = hg.Grid.unit_cube(n, 1.0, 1.0, 0.5, prec, "robin")
+        rho = I.blob_density_torch(n, I.draw_blobs(4, 3), "cuda", torch.float64)
+        rho_t = I.blob_density_torch(n, I.draw_blobs(4, 4), "cuda", torch.float64)
+        idx, w = HA.trilinear_probe_weights(grid, torch.from_numpy(I.probes(64, 11)))
+        with torch.no_grad():
+            target = (HA.potential(rho_t, grid, T).reshape(-1)[idx] * w).sum(1)
+
+        def step_loss(m, phi):
+            return (((phi.reshape(-1)[idx] * w).sum(1) - target) ** 2).sum()
+
+        def loss_plain(r):
+            return step_loss(T, HA.potential(r, grid, T))
+
+        r = {}
+        for name, K in [("no_checkpoints", None), ("K10", 10), ("K20", 20), ("K50", 50)]:
+            rr = rho.clone().requires_grad_(True)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            if K is None:
+                L = loss_plain(rr)
+            else:
+                L = HA.trajectory_loss(rr, grid, T, [T], step_loss, checkpoint_every=K)
+            L.backward()
+            torch.cuda.synchronize()
+            sec = time.perf_counter() - t0
+            mem = (grid.state_bytes() * int(np.ceil(T / K))) if K else 0
+            r[name] = {"forward_backward_s": round(sec, 4), "saved_state_bytes": mem}
+            if K is None:
+                grad = rr.grad.detach().cpu().numpy()
+            else:
+                g2 = rr.grad.detach().cpu().numpy()
+                r[name]["max_rel_diff_vs_no_checkpoints"] = float(np.abs(g2 - grad).max() / np.abs(grad).max())
+        rng = np.random.default_rng(17)
+        cells = [tuple(int(v) for v in rng.integers(0, n, 3)) for _ in range(32)]
+        errs = []
+        eps = 1e-2
+        for c in cells:
+            with torch.no_grad():
+                rp = rho.clone()
+                rp[c] += eps
+                rm = rho.clone()
+                rm[c] -= eps
+                fd = (loss_plain(rp) - loss_plain(rm)).item() / (2 * eps)
+            errs.append(abs(fd - grad[c]) / np.abs(grad).max())
+        r["fd_32_cells_max_err_rel_to_max_grad"] = float(max(errs))
+        r["full_trajectory_bytes"] = T * n ** 3 * 8
+        out["results"][prec] = r
+        grid.free()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -362,6 +524,9 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--cpu-substeps", type=int, default=6)
     ap.add_argument("--ref-substeps", type=int, default=1)
+    ap.add_argument("--config", choices=["headline", "precision", "batch", "adjoint"], default="headline",
+                    help="headline: the metric's 512^3 line (default); the others print the other workloads")
+    ap.add_argument("--substeps", type=int, default=None, help="sub-steps for --config precision/batch/adjoint")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -374,6 +539,16 @@ def main():
         return
     import paper_1602_05700_gb300 as hg
     hg.build()
+    if args.config != "headline":
+        defaults = {"precision": (256, 2000), "batch": (0, 500), "adjoint": (128, 400)}
+        n0, t0 = defaults[args.config]
+        if args.n == 512 and n0:
+            args.n = n0
+        args.substeps = args.substeps or t0
+        fn = {"precision": run_precision, "batch": run_batch, "adjoint": run_adjoint}[args.config]
+        if rank == 0:
+            print(json.dumps({"config": args.config, **fn(args)}), flush=True)
+        return
     line = run_ours(args, rank, world, local_rank)
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -144,11 +144,32 @@ int hg_get_moments(hg_grid* g, double* Q);
  */
 int hg_compare(hg_grid* g, const double* phi_P, int on_device, double out[3]);
 
-/* Checkpoint / resume of the full state (bit-exact): hg_state_bytes gives the size of the opaque host buffer
- * that hg_save_state fills and hg_load_state reads. */
+/* Checkpoint / resume of the full state (bit-exact): hg_state_bytes gives the size of the opaque buffer that
+ * hg_save_state fills and hg_load_state reads, in host memory (on_device = 0) or device memory (on_device = 1).
+ * A buffer is only valid for a grid of the same sizes, precision and boundary condition. */
 size_t hg_state_bytes(const hg_grid* g);
-int hg_save_state(hg_grid* g, void* host_buf);
-int hg_load_state(hg_grid* g, const void* host_buf);
+int hg_save_state(hg_grid* g, void* buf, int on_device);
+int hg_load_state(hg_grid* g, const void* buf, int on_device);
+
+/*
+ * Adjoint of the sub-stepping: dL/drho for a loss L of the potentials phi^m produced by hg_step from a fixed initial
+ * state (the paper has no adjoint; this is the transpose of the discretised Eq. HNeq.).  The sub-step is linear, so
+ * the reverse recursion needs no forward state:
+ *   hg_adjoint_reset(g)                   lambda = 0, running sum = 0 (the first call allocates a shadow state);
+ *   hg_adjoint_inject(g, dL/dphi^m, ...)  adds the direct derivative of L with respect to phi^m (interior cells,
+ *                                         nz*ny*nx values) at the current reverse level m;
+ *   hg_adjoint_step(g, n)                 n reverse sub-steps (m -> m - n), adding each level's lambda to the sum;
+ *   hg_adjoint_grad(g, out, ...)          out = dL/drho = -(c_h dt)^2 4 pi G sum_m lambda^m (minus its mean for
+ *                                         periodic boundaries), nz*ny*nx values.
+ * For L = L(phi^T) after T forward sub-steps: reset, inject(dL/dphi^T), step(T), grad.  For losses on several
+ * levels, inject each dL/dphi^m when the reverse sweep reaches m.  Dirichlet boundary data are treated as constants
+ * (their dependence on rho through the multipole moments is not differentiated); Robin ghosts and periodic copies
+ * are part of the state and are transposed exactly.  The adjoint state has the precision of the grid.
+ */
+int hg_adjoint_reset(hg_grid* g);
+int hg_adjoint_inject(hg_grid* g, const void* dL_dphi, int dtype, int on_device);
+int hg_adjoint_step(hg_grid* g, int n_substeps);
+int hg_adjoint_grad(hg_grid* g, void* dL_drho, int dtype, int on_device);
 
 /*
  * Measurement hooks.  hg_profile(g, 1) makes the library record a pair of CUDA events on the grid's stream around
@@ -165,6 +186,23 @@ int hg_sync(hg_grid* g);
 
 /* Release the grid and its device memory (NULL is allowed). */
 void hg_free(hg_grid* g);
+
+/*
+ * Batches: many independent grids (any sizes, both precisions, any boundary conditions) advanced together.  Every
+ * sub-step of all grids is one batched kernel launch (plus one batched ghost-copy launch if some grid is periodic);
+ * hg_batch_step records its n sub-steps once as a CUDA graph and replays it with one graph launch, on a stream of
+ * the batch that is ordered after, and before, the grids' own stream.  Results are bit-identical to hg_step on each
+ * grid (single sweeps: the grids' temporal depth is not used here).  The first hg_batch_step autotunes the z extent
+ * of a block by timing its first sub-steps (all candidates compute the same result) and caches the choice per
+ * device and set of grid shapes for the process.  All grids must live on one device and share one stream; a grid
+ * may belong to several batches and may also be stepped on its own between batch steps.
+ */
+typedef struct hg_batch hg_batch;
+int hg_batch_create(hg_grid* const* grids, int n, hg_batch** b);
+int hg_batch_step(hg_batch* b, int n_substeps);
+/* autotuned z planes per block (0 before the first hg_batch_step) and blocks per batched sub-step launch */
+int hg_batch_info(const hg_batch* b, int* z_planes_per_block, long long* blocks_per_substep);
+void hg_batch_free(hg_batch* b);
 
 /* Message of the last failing call on this host thread ("" if none). */
 const char* hg_last_error(void);

@@ -24,11 +24,11 @@ BC = {"dirichlet": HG_BC_DIRICHLET_ANALYTIC, "dirichlet_analytic": HG_BC_DIRICHL
       "robin": HG_BC_ROBIN, "periodic": HG_BC_PERIODIC}
 PREC = {"f32k": HG_PREC_F32K, "f64": HG_PREC_F64}
 
-__all__ = ["Grid", "HGError", "BC", "PREC", "build"]
+__all__ = ["Grid", "Batch", "HGError", "BC", "PREC", "build"]
 
 
 def build(force: bool = False) -> str:
-    from .build import build as _b
+    from .builder import build as _b
     return _b(force=force)
 
 
@@ -181,15 +181,46 @@ class Grid:
         _lib.check(_lib.lib().hg_compare(self.handle, p, dev, out))
         return float(out[0]), float(out[1]), float(out[2])
 
-    def save_state(self) -> bytes:
-        n = _lib.lib().hg_state_bytes(self.handle)
-        buf = ctypes.create_string_buffer(n)
-        _lib.check(_lib.lib().hg_save_state(self.handle, buf))
+    def state_bytes(self) -> int:
+        return int(_lib.lib().hg_state_bytes(self.handle))
+
+    def save_state(self, out=None):
+        """Checkpoint: bytes in host memory, or into `out` (a uint8 device tensor of state_bytes())."""
+        if out is not None:
+            _lib.check(_lib.lib().hg_save_state(self.handle, ctypes.c_void_p(out.data_ptr()), 1))
+            return out
+        buf = ctypes.create_string_buffer(self.state_bytes())
+        _lib.check(_lib.lib().hg_save_state(self.handle, buf, 0))
         return buf.raw
 
-    def load_state(self, blob: bytes) -> None:
+    def load_state(self, blob) -> None:
+        torch = _torch()
+        if isinstance(blob, torch.Tensor):
+            _lib.check(_lib.lib().hg_load_state(self.handle, ctypes.c_void_p(blob.data_ptr()), 1))
+            return
         buf = ctypes.create_string_buffer(blob, len(blob))
-        _lib.check(_lib.lib().hg_load_state(self.handle, buf))
+        _lib.check(_lib.lib().hg_load_state(self.handle, buf, 0))
+
+    # ---- adjoint (see hg.h) ----
+    def adjoint_reset(self):
+        _lib.check(_lib.lib().hg_adjoint_reset(self.handle))
+
+    def adjoint_inject(self, dL_dphi):
+        p, code, dev, keep = _buffer(dL_dphi)
+        self._check_size(keep)
+        _lib.check(_lib.lib().hg_adjoint_inject(self.handle, p, code, dev))
+
+    def adjoint_step(self, n=1):
+        _lib.check(_lib.lib().hg_adjoint_step(self.handle, int(n)))
+
+    def adjoint_grad(self, dtype=None):
+        """dL/drho as an (nz, ny, nx) device tensor."""
+        torch = _torch()
+        dtype = dtype or torch.float64
+        out = torch.empty(self.shape, dtype=dtype, device=self.device)
+        code = HG_DT_F64 if dtype == torch.float64 else HG_DT_F32
+        _lib.check(_lib.lib().hg_adjoint_grad(self.handle, ctypes.c_void_p(out.data_ptr()), code, 1))
+        return out
 
     def profile(self, enable=True):
         _lib.check(_lib.lib().hg_profile(self.handle, 1 if enable else 0))
@@ -218,3 +249,33 @@ class Grid:
         n = a.numel() if hasattr(a, "numel") else a.size
         if n != self.nx * self.ny * self.nz:
             raise HGError(-1, f"array has {n} values, grid has {self.nx * self.ny * self.nz} cells")
+
+
+class Batch:
+    """Several grids advanced together: one batched launch per sub-step, replayed from a CUDA graph."""
+
+    def __init__(self, grids):
+        self.grids = list(grids)
+        arr = (ctypes.c_void_p * len(self.grids))(*[g.handle for g in self.grids])
+        h = ctypes.c_void_p()
+        _lib.check(_lib.lib().hg_batch_create(arr, len(self.grids), ctypes.byref(h)))
+        self._h = h
+
+    def step(self, n=1):
+        _lib.check(_lib.lib().hg_batch_step(self._h, int(n)))
+
+    def info(self):
+        zb, nb = ctypes.c_int(), ctypes.c_longlong()
+        _lib.check(_lib.lib().hg_batch_info(self._h, ctypes.byref(zb), ctypes.byref(nb)))
+        return {"z_planes_per_block": zb.value, "blocks_per_substep": nb.value}
+
+    def free(self):
+        if getattr(self, "_h", None) is not None:
+            _lib.lib().hg_batch_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass

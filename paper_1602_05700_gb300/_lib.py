@@ -62,12 +62,20 @@ SIGNATURES = {
     "hg_get_moments": (_I, [_V, _P(_D)]),
     "hg_compare": (_I, [_V, _V, _I, _P(_D)]),
     "hg_state_bytes": (ctypes.c_size_t, [_V]),
-    "hg_save_state": (_I, [_V, _V]),
-    "hg_load_state": (_I, [_V, _V]),
+    "hg_save_state": (_I, [_V, _V, _I]),
+    "hg_load_state": (_I, [_V, _V, _I]),
+    "hg_adjoint_reset": (_I, [_V]),
+    "hg_adjoint_inject": (_I, [_V, _V, _I, _I]),
+    "hg_adjoint_step": (_I, [_V, _I]),
+    "hg_adjoint_grad": (_I, [_V, _V, _I, _I]),
     "hg_profile": (_I, [_V, _I]),
     "hg_profile_read": (_I, [_V, _P(_D), _P(ctypes.c_longlong), _P(ctypes.c_longlong)]),
     "hg_sync": (_I, [_V]),
     "hg_free": (None, [_V]),
+    "hg_batch_create": (_I, [_P(_V), _I, _P(_V)]),
+    "hg_batch_step": (_I, [_V, _I]),
+    "hg_batch_info": (_I, [_V, _P(_I), _P(ctypes.c_longlong)]),
+    "hg_batch_free": (None, [_V]),
     "hg_last_error": (ctypes.c_char_p, []),
 }
 
@@ -79,7 +87,7 @@ def lib():
     global _lib
     if _lib is None:
         if not os.path.exists(LIB_PATH):
-            raise RuntimeError(f"CUDA library {LIB_PATH} is missing: run paper_1602_05700_gb300.build.build() "
+            raise RuntimeError(f"CUDA library {LIB_PATH} is missing: run paper_1602_05700_gb300.build() "
                                "(or __graft_entry__.build()) first")
         L = ctypes.CDLL(LIB_PATH)
         for name, (res, args) in SIGNATURES.items():

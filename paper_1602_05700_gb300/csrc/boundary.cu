@@ -194,9 +194,7 @@ __global__ void k_robin_static(int prec, void* p, void* lo, Layout L, Faces F, c
 }
 
 // periodic copy into the face ghosts of one time level
-__global__ void k_periodic(int prec, void* p, void* lo, Layout L, Faces F) {
-    long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (t >= F.off[6]) return;
+__device__ __forceinline__ void periodic_ghost(int prec, void* p, void* lo, const Layout& L, const Faces& F, long long t) {
     int gc[3], ic[3];
     int f = face_cell(F, L.nx, L.ny, L.nz, t, gc, ic);
     int src[3] = {gc[0], gc[1], gc[2]};
@@ -209,6 +207,29 @@ __global__ void k_periodic(int prec, void* p, void* lo, Layout L, Faces F) {
         ((float*)p)[qg] = ((const float*)p)[qs];
         ((float*)lo)[qg] = ((const float*)lo)[qs];
     }
+}
+
+__global__ void k_periodic(int prec, void* p, void* lo, Layout L, Faces F) {
+    long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= F.off[6]) return;
+    periodic_ghost(prec, p, lo, L, F, t);
+}
+
+// periodic copies for several grids in one launch: ghost t of the concatenation belongs to the entry e with
+// first[e] <= t < first[e+1]
+__global__ void k_periodic_batch(const PeriodicArgs* __restrict__ tab, const long long* __restrict__ first, int n) {
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= first[n]) return;
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (first[mid] <= t)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    const PeriodicArgs& A = tab[lo];
+    periodic_ghost(A.prec, A.p, A.lo, A.L, A.F, t - first[lo]);
 }
 
 template <int LMAX>
@@ -275,14 +296,23 @@ int set_ghosts_dirichlet(hg_grid* g) {
     }
 }
 
-// periodic copies into the face ghosts of the level just written by a single sweep (buffer 1 - cur)
-int launch_periodic_copy(hg_grid* g) {
+// periodic copies into the face ghosts of time-level buffer b (1 - cur: the level a single sweep just wrote)
+int launch_periodic_fill(hg_grid* g, int b) {
     long long n = g->F.off[6];
     int threads = 256;
     unsigned blocks = (unsigned)((n + threads - 1) / threads);
-    int nxt = 1 - g->cur;
-    k_periodic<<<blocks, threads, 0, g->stream>>>(g->prec, g->phi[nxt], g->lo[nxt], g->L, g->F);
+    k_periodic<<<blocks, threads, 0, g->stream>>>(g->prec, g->phi[b], g->lo[b], g->L, g->F);
     HG_LAUNCHED("periodic ghost kernel");
+    return HG_OK;
+}
+
+int launch_periodic_copy(hg_grid* g) { return launch_periodic_fill(g, 1 - g->cur); }
+
+int launch_periodic_batch(cudaStream_t st, const PeriodicArgs* tab, const long long* first, int n, long long total) {
+    if (total <= 0) return HG_OK;
+    k_periodic_batch<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(tab, first, n);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "batched periodic ghost kernel");
     return HG_OK;
 }
 

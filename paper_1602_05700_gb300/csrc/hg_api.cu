@@ -92,9 +92,12 @@ static int build_robin(hg_grid* g) {
     return HG_OK;
 }
 
+extern "C" void hg_free(hg_grid* g);
+
 static void release(hg_grid* g) {
+    if (g->adj) hg_free(g->adj);
     void* ptrs[] = {g->phi[0], g->phi[1], g->lo[0], g->lo[1], g->dlt[0], g->dlt[1], g->rho, g->robin, g->robin32,
-                    g->red, g->dres, g->staging};
+                    g->red, g->dres, g->staging, g->acc[0], g->acc[1]};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (g->prof_ev) {
@@ -421,10 +424,11 @@ size_t hg_state_bytes(const hg_grid* g) {
     return sizeof(StateHeader) + (size_t)n_buffers(g) * (size_t)g->L.elems * g->esize;
 }
 
-int hg_save_state(hg_grid* g, void* host_buf) {
+int hg_save_state(hg_grid* g, void* buf, int on_device) {
     int rc = check_grid(g);
     if (rc) return rc;
-    if (!host_buf) return fail(HG_ERR_ARG, "null buffer");
+    if (!buf) return fail(HG_ERR_ARG, "null buffer");
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     StateHeader H;
     memset(&H, 0, sizeof H);
     memcpy(H.magic, "HGSTATE1", 8);
@@ -440,29 +444,36 @@ int hg_save_state(hg_grid* g, void* host_buf) {
     H.mass = g->mass;
     H.rho_bar = g->rho_bar;
     memcpy(H.Q, g->Q, sizeof H.Q);
-    memcpy(host_buf, &H, sizeof H);
-    char* p = (char*)host_buf + sizeof H;
+    if (on_device)
+        HG_CUDA(cudaMemcpyAsync(buf, &H, sizeof H, cudaMemcpyHostToDevice, g->stream));
+    else
+        memcpy(buf, &H, sizeof H);
+    char* p = (char*)buf + sizeof H;
     size_t bytes = (size_t)g->L.elems * g->esize;
-    for (int b = 0; b < n_buffers(g); ++b, p += bytes)
-        HG_CUDA(cudaMemcpyAsync(p, *buffer(g, b), bytes, cudaMemcpyDeviceToHost, g->stream));
-    HG_CUDA(cudaStreamSynchronize(g->stream));
+    for (int b = 0; b < n_buffers(g); ++b, p += bytes) HG_CUDA(cudaMemcpyAsync(p, *buffer(g, b), bytes, kind, g->stream));
+    HG_CUDA(cudaStreamSynchronize(g->stream));  // the header copy reads a stack variable
     return HG_OK;
 }
 
-int hg_load_state(hg_grid* g, const void* host_buf) {
+int hg_load_state(hg_grid* g, const void* buf, int on_device) {
     int rc = check_grid(g);
     if (rc) return rc;
-    if (!host_buf) return fail(HG_ERR_ARG, "null buffer");
+    if (!buf) return fail(HG_ERR_ARG, "null buffer");
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     StateHeader H;
-    memcpy(&H, host_buf, sizeof H);
+    if (on_device) {
+        HG_CUDA(cudaMemcpyAsync(&H, buf, sizeof H, cudaMemcpyDeviceToHost, g->stream));
+        HG_CUDA(cudaStreamSynchronize(g->stream));
+    } else {
+        memcpy(&H, buf, sizeof H);
+    }
     if (memcmp(H.magic, "HGSTATE1", 8) != 0 || H.nx != g->nx || H.ny != g->ny || H.nz != g->nz || H.prec != g->prec ||
         H.bc != g->bc || H.lmax != g->lmax)
         return fail(HG_ERR_ARG, "state buffer does not match this grid");
-    const char* p = (const char*)host_buf + sizeof H;
+    const char* p = (const char*)buf + sizeof H;
     size_t bytes = (size_t)g->L.elems * g->esize;
-    for (int b = 0; b < n_buffers(g); ++b, p += bytes)
-        HG_CUDA(cudaMemcpyAsync(*buffer(g, b), p, bytes, cudaMemcpyHostToDevice, g->stream));
-    HG_CUDA(cudaStreamSynchronize(g->stream));
+    for (int b = 0; b < n_buffers(g); ++b, p += bytes) HG_CUDA(cudaMemcpyAsync(*buffer(g, b), p, bytes, kind, g->stream));
+    if (!on_device) HG_CUDA(cudaStreamSynchronize(g->stream));
     g->cur = H.cur;
     g->have_Q = H.have_Q;
     g->step = H.step;
@@ -493,6 +504,85 @@ int hg_profile_read(hg_grid* g, double* substep_kernel_ms, long long* substep_la
     if (kernel_launches) *kernel_launches = g->launches;
     g->prof_ms = 0.0;
     g->prof_count = 0;
+    return HG_OK;
+}
+
+// ---- adjoint ----
+int hg_adjoint_reset(hg_grid* g) {
+    int rc = check_grid(g);
+    if (rc) return rc;
+    if (!g->adj) {
+        // Dirichlet data do not depend on rho in the adjoint: the shadow grid keeps zero boundary data (no density is
+        // ever set on it, so its source is zero as well)
+        const int bc = (g->bc == HG_BC_DIRICHLET_MULTIPOLE) ? HG_BC_DIRICHLET_ANALYTIC : g->bc;
+        if ((rc = hg_init_grid(&g->adj, g->nx, g->ny, g->nz, g->h, g->origin, g->c, g->G, g->dt, g->prec, bc, 0,
+                               g->stream)))
+            return rc;
+        const size_t bytes = (size_t)g->L.elems * g->esize;
+        HG_CUDA(cudaMalloc(&g->acc[0], bytes));
+        if (g->prec == HG_PREC_F32K) HG_CUDA(cudaMalloc(&g->acc[1], bytes));
+    }
+    hg_grid* a = g->adj;
+    const size_t bytes = (size_t)a->L.elems * a->esize;
+    void* bufs[] = {a->phi[0], a->phi[1], a->lo[0], a->lo[1], a->dlt[0], a->dlt[1], g->acc[0], g->acc[1]};
+    for (void* b : bufs)
+        if (b) HG_CUDA(cudaMemsetAsync(b, 0, bytes, g->stream));
+    a->cur = 0;
+    a->dcur = 0;
+    a->step = 0;
+    return HG_OK;
+}
+
+int hg_adjoint_inject(hg_grid* g, const void* dL_dphi, int dtype, int on_device) {
+    int rc = check_grid(g);
+    if (rc) return rc;
+    if (!g->adj) return fail(HG_ERR_STATE, "call hg_adjoint_reset first");
+    if (!dL_dphi) return fail(HG_ERR_ARG, "null input");
+    if (dtype != HG_DT_F32 && dtype != HG_DT_F64) return fail(HG_ERR_ARG, "unknown dtype %d", dtype);
+    hg_grid* a = g->adj;
+    const void* v = dL_dphi;
+    if (!on_device) {
+        if ((rc = ensure_staging(a))) return rc;
+        HG_CUDA(cudaMemcpyAsync(a->staging, dL_dphi, (size_t)a->nx * a->ny * a->nz * dt_size(dtype),
+                                cudaMemcpyHostToDevice, a->stream));
+        v = a->staging;
+    }
+    if ((rc = adjoint_inject(a, v, dtype))) return rc;
+    // the ghosts of a periodic level are copies of its interior, so they follow the injection
+    if (a->bc == HG_BC_PERIODIC && (rc = launch_periodic_fill(a, a->cur))) return rc;
+    if (!on_device) HG_CUDA(cudaStreamSynchronize(a->stream));
+    return HG_OK;
+}
+
+int hg_adjoint_step(hg_grid* g, int n_substeps) {
+    int rc = check_grid(g);
+    if (rc) return rc;
+    if (!g->adj) return fail(HG_ERR_STATE, "call hg_adjoint_reset first");
+    if (n_substeps < 0) return fail(HG_ERR_ARG, "n_substeps must be >= 0");
+    hg_grid* a = g->adj;
+    for (int s = 0; s < n_substeps; ++s) {
+        if ((rc = adjoint_accumulate(a, g->acc[0], g->acc[1]))) return rc;
+        if ((rc = launch_step_single(a))) return rc;
+        if (a->bc == HG_BC_PERIODIC && (rc = launch_periodic_copy(a))) return rc;
+        a->cur = 1 - a->cur;
+        ++a->step;
+    }
+    return HG_OK;
+}
+
+int hg_adjoint_grad(hg_grid* g, void* dL_drho, int dtype, int on_device) {
+    int rc = check_grid(g);
+    if (rc) return rc;
+    if (!g->adj) return fail(HG_ERR_STATE, "call hg_adjoint_reset first");
+    if (!dL_drho) return fail(HG_ERR_ARG, "null output");
+    if (dtype != HG_DT_F32 && dtype != HG_DT_F64) return fail(HG_ERR_ARG, "unknown dtype %d", dtype);
+    hg_grid* a = g->adj;
+    if (on_device) return adjoint_gradient(a, g->acc[0], g->acc[1], dL_drho, dtype, a->red);
+    if ((rc = ensure_staging(a))) return rc;
+    if ((rc = adjoint_gradient(a, g->acc[0], g->acc[1], a->staging, dtype, a->red))) return rc;
+    HG_CUDA(cudaMemcpyAsync(dL_drho, a->staging, (size_t)a->nx * a->ny * a->nz * dt_size(dtype),
+                            cudaMemcpyDeviceToHost, a->stream));
+    HG_CUDA(cudaStreamSynchronize(a->stream));
     return HG_OK;
 }
 

@@ -126,6 +126,7 @@ struct hg_grid {
     double mass, rho_bar;
     long long step;
     int tdepth;
+    int zb;  // z planes per block of the single sweep (0 = default rule; set by the batch autotuner)
     hg::YlmNorm ylm;
     // measurement: kernel launch count and CUDA events around the sub-step kernel
     long long launches;
@@ -134,6 +135,10 @@ struct hg_grid {
     double prof_ms;         // folded time
     long long prof_count;   // folded launches
     cudaEvent_t* prof_ev;   // 2 * kProfPairs events, created when profiling is first enabled
+    // adjoint: a shadow grid (same geometry, precision, boundary condition; zero boundary data and source) that
+    // carries lambda, and the running sum of lambda over the reverse sub-steps (float pair or double, padded layout)
+    hg_grid* adj;
+    void* acc[2];
 };
 
 namespace hg {
@@ -156,7 +161,11 @@ int cuda_fail(cudaError_t e, const char* what);
 
 // kernels' host launchers (each returns HG_OK or an error code)
 int launch_step_single(hg_grid* g);                  // one interior sweep: cur -> 1-cur (stencil.cu)
+int adjoint_inject(hg_grid* a, const void* v, int vdt);
+int adjoint_accumulate(hg_grid* a, void* acc_a, void* acc_b);
+int adjoint_gradient(hg_grid* a, const void* acc_a, const void* acc_b, void* out, int odt, double* scratch);
 int launch_periodic_copy(hg_grid* g);                // periodic ghosts of the new level after a single sweep
+int launch_periodic_fill(hg_grid* g, int b);         // periodic ghosts of time-level buffer b
 int launch_temporal(hg_grid* g, int k);              // k fused sub-steps: cur -> 1-cur (temporal.cu)
 int ensure_staging(hg_grid* g);
 int prepare_source(hg_grid* g, const void* src, int dtype, double* sum_host);  // dense rho -> stored s
@@ -174,6 +183,44 @@ constexpr int kProfPairs = 4096;
 int prof_begin(hg_grid* g);  // record the start event of a sub-step kernel launch (no-op unless profiling)
 int prof_end(hg_grid* g);
 int prof_fold(hg_grid* g);   // synchronise and add the recorded pairs to prof_ms
+
+// ---- sweep arguments (stencil.cu) ----
+struct Bnd {
+    int faces;              // 1: Robin ghosts to update
+    const float2* robin32;  // (alpha, beta) per face ghost, compensated float grids
+    const double* robin;    // (alpha, beta, gamma) per face ghost, FP64 grids
+    long long off[7];       // face offsets in the ghost enumeration (hg::Faces)
+};
+
+// Everything one sweep of one grid needs (a launch of one grid, or one entry of a batched launch).
+struct SweepArgs {
+    const void* hi_c;  // phi^n: F64 values, or the float part (F32K)
+    const void* lo_c;  // F32K compensation of phi^n
+    void* hi_n;        // level n+1 (F64: written over phi^{n-1})
+    void* lo_n;
+    void* dlt;         // F32K phi^n - phi^{n-1}, updated in place
+    const void* rho;   // scaled source s
+    Layout L;
+    double nu2;
+    int zb;            // z planes per block
+    int prec;
+    unsigned gx, gy;   // blocks in x and y of this grid's sweep
+    Bnd B;
+};
+
+// periodic ghost copies of one time level of one grid (an entry of a batched copy)
+struct PeriodicArgs {
+    int prec;
+    void* p;
+    void* lo;
+    Layout L;
+    Faces F;
+};
+int launch_periodic_batch(cudaStream_t st, const PeriodicArgs* tab, const long long* first, int n, long long total);
+
+SweepArgs sweep_args(const hg_grid* g, int zb);  // sub-step cur -> 1 - cur of grid g; zb = 0: default z chunk
+unsigned sweep_blocks(const SweepArgs& A);
+int launch_step_batch(cudaStream_t st, const SweepArgs* tab, const unsigned* first, int n, unsigned total_blocks);
 
 // ---- deterministic reductions --------------------------------------------------------------------------------
 constexpr int kRedThreads = 256;

@@ -38,78 +38,100 @@ __device__ __forceinline__ void set(float4& v, int e, float x) {
     if (e == 0) v.x = x; else if (e == 1) v.y = x; else if (e == 2) v.z = x; else v.w = x;
 }
 
-// Robin boundary work rides in the same launch: when `faces` is set, the first z-slice of blocks (scheduled first,
-// so it overlaps the sweep) updates every face ghost to level n+1 from level-n values only (the ghost and its
-// interior neighbour), which no other block of the launch writes.  The sweep blocks themselves carry no boundary
-// code, so the interior path keeps its registers and its memory pipeline.  Dirichlet ghosts are data; periodic
-// copies of the new level are made by a small kernel after the sweep (boundary.cu).
-struct Bnd {
-    int faces;              // 1: Robin ghost blocks present (blockIdx.z == 0)
-    const float2* robin32;  // (alpha, beta) per face ghost, compensated float grids
-    const double* robin;    // (alpha, beta, gamma) per face ghost, FP64 grids
-    long long off[7];       // face offsets in the ghost enumeration (hg::Faces)
+// Robin boundary work rides in the same launch, after each block's z-march (so it adds no registers to the sweep):
+// a block next to a face updates the face ghosts that border its own cells -- its rows and planes of an x face, its
+// x range and planes of a y face, its x range and rows of a z face -- to level n+1, from level-n values only (the
+// ghost and its interior neighbour), which no block of the launch writes.  Every face ghost belongs to exactly one
+// block.  Dirichlet ghosts are data; periodic copies of the new level are made by a small kernel after the sweep
+// (boundary.cu).
+
+
+
+
+// The face ghosts owned by this block, handed to upd in batches of up to 4 (padded index of the ghost, of its
+// interior neighbour, ghost number), so that the loads of a batch are issued together.
+constexpr int kGB = 4;
+struct GhostBatch {
+    long long qg[kGB], qi[kGB], t[kGB];
+    int n;
 };
 
-// face ghost t -> padded indices of the ghost and of its interior neighbour (32-bit in-face arithmetic)
-__device__ __forceinline__ void face_pair(const Layout& L, const Bnd& B, long long t, long long& qg, long long& qi) {
-    // face index and offset by comparisons (no dynamic indexing of the parameter array, which would go to local
-    // memory)
-    long long base = 0;
-    int f = 0;
+template <class Where, class Upd>
+__device__ __forceinline__ void batched(int count, int tid, int nth, Where&& where, Upd&& upd) {
+    for (int base = tid; base < count; base += kGB * nth) {
+        GhostBatch gb;
+        gb.n = 0;
 #pragma unroll
-    for (int u = 1; u < 6; ++u)
-        if (t >= B.off[u]) {
-            f = u;
-            base = B.off[u];
+        for (int u = 0; u < kGB; ++u) {
+            const int t = base + u * nth;
+            if (t < count) {
+                where(t, gb.qg[u], gb.qi[u], gb.t[u]);
+                gb.n = u + 1;
+            }
         }
-    const int r = (int)(t - base);
-    const int na = f < 2 ? L.ny : L.nx;
-    const int a = r % na, b = r / na;
-    switch (f) {
-        case 0: qg = L.at(-1, a, b); qi = qg + 1; break;
-        case 1: qg = L.at(L.nx, a, b); qi = qg - 1; break;
-        case 2: qg = L.at(a, -1, b); qi = qg + L.pitch; break;
-        case 3: qg = L.at(a, L.ny, b); qi = qg - L.pitch; break;
-        case 4: qg = L.at(a, b, -1); qi = qg + L.plane; break;
-        default: qg = L.at(a, b, L.nz); qi = qg - L.plane; break;
+        upd(gb);
     }
 }
 
-__device__ __forceinline__ long long face_thread(long long& stride) {
-    stride = (long long)gridDim.x * gridDim.y * blockDim.x * blockDim.y;
-    return ((long long)blockIdx.y * gridDim.x + blockIdx.x) * (blockDim.x * blockDim.y) + threadIdx.y * blockDim.x +
-           threadIdx.x;
+template <class Upd>
+__device__ __forceinline__ void block_face_ghosts(const Layout& L, const Bnd& B, int x0, int j0, int wy, int k0, int k1,
+                                                  int bx, int by, int gx, int gy, Upd&& upd) {
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x, nth = blockDim.x * blockDim.y;
+    const int jn = min(wy, L.ny - j0), xn = min(128, L.nx - x0), kn = k1 - k0;
+    if (bx == 0)
+        batched(jn * kn, tid, nth, [&](int t, long long& qg, long long& qi, long long& r) {
+            const int j = j0 + t % jn, k = k0 + t / jn;
+            qg = L.at(-1, j, k), qi = qg + 1, r = B.off[0] + (long long)k * L.ny + j;
+        }, upd);
+    if (bx == gx - 1)
+        batched(jn * kn, tid, nth, [&](int t, long long& qg, long long& qi, long long& r) {
+            const int j = j0 + t % jn, k = k0 + t / jn;
+            qg = L.at(L.nx, j, k), qi = qg - 1, r = B.off[1] + (long long)k * L.ny + j;
+        }, upd);
+    if (by == 0)
+        batched(xn * kn, tid, nth, [&](int t, long long& qg, long long& qi, long long& r) {
+            const int i = x0 + t % xn, k = k0 + t / xn;
+            qg = L.at(i, -1, k), qi = qg + L.pitch, r = B.off[2] + (long long)k * L.nx + i;
+        }, upd);
+    if (by == gy - 1)
+        batched(xn * kn, tid, nth, [&](int t, long long& qg, long long& qi, long long& r) {
+            const int i = x0 + t % xn, k = k0 + t / xn;
+            qg = L.at(i, L.ny, k), qi = qg - L.pitch, r = B.off[3] + (long long)k * L.nx + i;
+        }, upd);
+    if (k0 == 0)
+        batched(xn * jn, tid, nth, [&](int t, long long& qg, long long& qi, long long& r) {
+            const int i = x0 + t % xn, j = j0 + t / xn;
+            qg = L.at(i, j, -1), qi = qg + L.plane, r = B.off[4] + (long long)j * L.nx + i;
+        }, upd);
+    if (k1 == L.nz)
+        batched(xn * jn, tid, nth, [&](int t, long long& qg, long long& qi, long long& r) {
+            const int i = x0 + t % xn, j = j0 + t / xn;
+            qg = L.at(i, j, L.nz), qi = qg - L.plane, r = B.off[5] + (long long)j * L.nx + i;
+        }, upd);
 }
 
 template <int WY>
-__global__ void __launch_bounds__(32 * WY) k_step_f32k(const float* __restrict__ hi_c, const float* __restrict__ lo_c,
-                                                       float* __restrict__ hi_n, float* __restrict__ lo_n,
-                                                       float* __restrict__ dlt, const float* __restrict__ rho, Layout L,
-                                                       float nu2, int zb, Bnd B) {
-    if (B.faces && blockIdx.z == 0) {  // Robin ghosts of level n+1
-        long long stride;
-        for (long long t = face_thread(stride); t < B.off[6]; t += stride) {
-            long long qg, qi;
-            face_pair(L, B, t, qg, qi);
-            const float2 ab = B.robin32[t];
-            float gh, gl;
-            robin_update_f32k(ab.x, ab.y, __ldg(hi_c + qg), __ldg(lo_c + qg), __ldg(hi_c + qi), __ldg(lo_c + qi), gh, gl);
-            hi_n[qg] = gh;
-            lo_n[qg] = gl;
-        }
-        return;
-    }
+__device__ __forceinline__ void sweep_f32k(const SweepArgs& A, int bx, int by, int bz) {
+    const float* __restrict__ hi_c = (const float*)A.hi_c;
+    const float* __restrict__ lo_c = (const float*)A.lo_c;
+    float* __restrict__ hi_n = (float*)A.hi_n;
+    float* __restrict__ lo_n = (float*)A.lo_n;
+    float* __restrict__ dlt = (float*)A.dlt;
+    const float* __restrict__ rho = (const float*)A.rho;
+    const Layout& L = A.L;
+    const Bnd& B = A.B;
+    const float nu2 = (float)A.nu2;
+    const int zb = A.zb;
     const int lane = threadIdx.x;
-    const int j = blockIdx.y * WY + threadIdx.y;
-    if (j >= L.ny) return;  // whole warp
-    const int i0 = blockIdx.x * 128 + lane * 4;
+    const int j = by * WY + threadIdx.y;
+    const int i0 = bx * 128 + lane * 4;
     const bool active = i0 < L.nx;  // this lane owns cells
     const bool halo = i0 <= L.nx;   // this lane's group holds cells or the +x ghost (read for its left neighbour)
     const bool full = i0 + 3 < L.nx;
-    const int k0 = (blockIdx.z - B.faces) * zb;
+    const int k0 = bz * zb;
     const int k1 = min(L.nz, k0 + zb);
     const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-
+    if (j < L.ny) {  // whole warps: rows past ny only join the boundary epilogue
     long long q = L.at(i0, j, k0);
     float4 hm = z4, hc = z4, lm = z4, lc = z4;
     if (halo) {
@@ -185,6 +207,29 @@ __global__ void __launch_bounds__(32 * WY) k_step_f32k(const float* __restrict__
         lm = lc;
         lc = lp;
     }
+    }
+    if (B.faces)
+        block_face_ghosts(L, B, bx * 128, by * WY, WY, k0, k1, bx, by, A.gx, A.gy, [&](const GhostBatch& gb) {
+            float hg[kGB], lg[kGB], hin[kGB], lin[kGB];
+            float2 ab[kGB];
+#pragma unroll
+            for (int u = 0; u < kGB; ++u)
+                if (u < gb.n) {
+                    ab[u] = B.robin32[gb.t[u]];
+                    hg[u] = __ldg(hi_c + gb.qg[u]);
+                    lg[u] = __ldg(lo_c + gb.qg[u]);
+                    hin[u] = __ldg(hi_c + gb.qi[u]);
+                    lin[u] = __ldg(lo_c + gb.qi[u]);
+                }
+#pragma unroll
+            for (int u = 0; u < kGB; ++u)
+                if (u < gb.n) {
+                    float gh, gl;
+                    robin_update_f32k(ab[u].x, ab[u].y, hg[u], lg[u], hin[u], lin[u], gh, gl);
+                    hi_n[gb.qg[u]] = gh;
+                    lo_n[gb.qg[u]] = gl;
+                }
+        });
 }
 
 // f64: 4 cells per lane as two double2 (arithmetic in cell.cuh)
@@ -211,30 +256,26 @@ __device__ __forceinline__ D4 ldd4rw(const double* p) {
 }
 
 template <int WY>
-__global__ void __launch_bounds__(32 * WY, 3) k_step_f64(const double* __restrict__ phi_c, double* __restrict__ phi_pn,
-                                                      const double* __restrict__ rho, Layout L, double nu2, int zb,
-                                                      Bnd B) {
-    if (B.faces && blockIdx.z == 0) {  // Robin ghosts of level n+1
-        long long stride;
-        for (long long t = face_thread(stride); t < B.off[6]; t += stride) {
-            long long qg, qi;
-            face_pair(L, B, t, qg, qi);
-            phi_pn[qg] = robin_update(B.robin[3 * t], B.robin[3 * t + 1], __ldg(phi_c + qg), __ldg(phi_c + qi));
-        }
-        return;
-    }
+__device__ __forceinline__ void sweep_f64(const SweepArgs& A, int bx, int by, int bz) {
+    const double* __restrict__ phi_c = (const double*)A.hi_c;
+    double* __restrict__ phi_pn = (double*)A.hi_n;
+    const double* __restrict__ rho = (const double*)A.rho;
+    const Layout& L = A.L;
+    const Bnd& B = A.B;
+    const double nu2 = A.nu2;
+    const int zb = A.zb;
     const int lane = threadIdx.x;
-    const int j = blockIdx.y * WY + threadIdx.y;
-    if (j >= L.ny) return;
-    const int i0 = blockIdx.x * 128 + lane * 4;
+    const int j = by * WY + threadIdx.y;
+    const int i0 = bx * 128 + lane * 4;
     const bool active = i0 < L.nx;  // this lane owns cells
     const bool halo = i0 <= L.nx;   // this lane's group holds cells or the +x ghost
     const bool full = i0 + 3 < L.nx;
-    const int k0 = (blockIdx.z - B.faces) * zb;
+    const int k0 = bz * zb;
     const int k1 = min(L.nz, k0 + zb);
     D4 zero;
 #pragma unroll
     for (int e = 0; e < 4; ++e) zero.v[e] = 0.0;
+    if (j < L.ny) {  // whole warps: rows past ny only join the boundary epilogue
     long long q = L.at(i0, j, k0);
     D4 cm = zero, cc = zero;
     if (halo) {
@@ -277,6 +318,22 @@ __global__ void __launch_bounds__(32 * WY, 3) k_step_f64(const double* __restric
         cm = cc;
         cc = cp;
     }
+    }
+    if (B.faces)
+        block_face_ghosts(L, B, bx * 128, by * WY, WY, k0, k1, bx, by, A.gx, A.gy, [&](const GhostBatch& gb) {
+            double a[kGB], b[kGB], pg[kGB], pi[kGB];
+#pragma unroll
+            for (int u = 0; u < kGB; ++u)
+                if (u < gb.n) {
+                    a[u] = B.robin[3 * gb.t[u]];
+                    b[u] = B.robin[3 * gb.t[u] + 1];
+                    pg[u] = __ldg(phi_c + gb.qg[u]);
+                    pi[u] = __ldg(phi_c + gb.qi[u]);
+                }
+#pragma unroll
+            for (int u = 0; u < kGB; ++u)
+                if (u < gb.n) phi_pn[gb.qg[u]] = robin_update(a[u], b[u], pg[u], pi[u]);
+        });
 }
 
 constexpr int kWY = 8;
@@ -293,31 +350,86 @@ int zchunk(const hg_grid* g) {
     return zb;
 }
 
+template <int WY>
+__global__ void __launch_bounds__(32 * WY, 3) k_step_f32k(const SweepArgs A) {
+    sweep_f32k<WY>(A, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
+template <int WY>
+__global__ void __launch_bounds__(32 * WY, 3) k_step_f64(const SweepArgs A) {
+    sweep_f64<WY>(A, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
+// One launch for the sub-step of many grids: block b belongs to the grid g with first[g] <= b < first[g+1]
+// (binary search in the prefix table), and runs that grid's sweep body for its local block coordinates.  Grids of
+// both precisions mix in one launch (the branch is uniform per block).
+template <int WY>
+__global__ void __launch_bounds__(32 * WY, 3) k_step_batch(const SweepArgs* __restrict__ tab,
+                                                           const unsigned* __restrict__ first, int n) {
+    const unsigned b = blockIdx.x;
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(first + mid) <= b)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    const SweepArgs& A = tab[lo];
+    const unsigned local = b - __ldg(first + lo);
+    const int bx = (int)(local % A.gx), by = (int)((local / A.gx) % A.gy), bz = (int)(local / (A.gx * A.gy));
+    if (A.prec == HG_PREC_F32K)
+        sweep_f32k<WY>(A, bx, by, bz);
+    else
+        sweep_f64<WY>(A, bx, by, bz);
+}
+
 }  // namespace
 
+// the sweep arguments of grid g for the sub-step cur -> 1 - cur, with z chunks of zb planes (0 = default rule)
+SweepArgs sweep_args(const hg_grid* g, int zb) {
+    SweepArgs A;
+    const int nxt = 1 - g->cur;
+    A.hi_c = g->phi[g->cur];
+    A.lo_c = g->lo[g->cur];
+    A.hi_n = g->phi[nxt];
+    A.lo_n = g->lo[nxt];
+    A.dlt = g->dlt[g->dcur];
+    A.rho = g->rho;
+    A.L = g->L;
+    A.nu2 = g->nu2;
+    A.zb = zb > 0 ? (zb < g->nz ? zb : g->nz) : zchunk(g);
+    A.prec = g->prec;
+    A.gx = (g->nx + 127) / 128;
+    A.gy = (g->ny + kWY - 1) / kWY;
+    A.B.faces = g->bc == HG_BC_ROBIN ? 1 : 0;
+    A.B.robin32 = g->robin32;
+    A.B.robin = g->robin;
+    for (int f = 0; f < 7; ++f) A.B.off[f] = g->F.off[f];
+    return A;
+}
+
+unsigned sweep_blocks(const SweepArgs& A) { return A.gx * A.gy * (unsigned)((A.L.nz + A.zb - 1) / A.zb); }
+
 int launch_step_single(hg_grid* g) {
-    const Layout& L = g->L;
-    int zb = zchunk(g);
+    const SweepArgs A = sweep_args(g, g->zb);
     dim3 block(32, kWY);
-    Bnd B;
-    B.faces = g->bc == HG_BC_ROBIN ? 1 : 0;
-    B.robin32 = g->robin32;
-    B.robin = g->robin;
-    for (int f = 0; f < 7; ++f) B.off[f] = g->F.off[f];
-    dim3 grid((g->nx + 127) / 128, (g->ny + kWY - 1) / kWY, (g->nz + zb - 1) / zb + B.faces);
-    int nxt = 1 - g->cur;
+    dim3 grid(A.gx, A.gy, (g->nz + A.zb - 1) / A.zb);
     int rc = prof_begin(g);
     if (rc) return rc;
-    if (g->prec == HG_PREC_F32K) {
-        k_step_f32k<kWY><<<grid, block, 0, g->stream>>>(
-            (const float*)g->phi[g->cur], (const float*)g->lo[g->cur], (float*)g->phi[nxt], (float*)g->lo[nxt],
-            (float*)g->dlt[g->dcur], (const float*)g->rho, L, (float)g->nu2, zb, B);
-    } else {
-        k_step_f64<kWY><<<grid, block, 0, g->stream>>>((const double*)g->phi[g->cur], (double*)g->phi[nxt],
-                                                       (const double*)g->rho, L, g->nu2, zb, B);
-    }
+    if (g->prec == HG_PREC_F32K)
+        k_step_f32k<kWY><<<grid, block, 0, g->stream>>>(A);
+    else
+        k_step_f64<kWY><<<grid, block, 0, g->stream>>>(A);
     HG_LAUNCHED("stencil sub-step kernel");
     return prof_end(g);
+}
+
+int launch_step_batch(cudaStream_t st, const SweepArgs* tab, const unsigned* first, int n, unsigned total_blocks) {
+    k_step_batch<kWY><<<total_blocks, dim3(32, kWY), 0, st>>>(tab, first, n);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "batched sub-step kernel");
+    return HG_OK;
 }
 
 }  // namespace hg

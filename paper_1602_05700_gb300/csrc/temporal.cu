@@ -50,9 +50,8 @@ __device__ __forceinline__ int wrap(int v, int n) {
 }
 
 template <int K>
-__global__ void __launch_bounds__(TB* TB, 1) k_temporal_f32k(const TParams P) {
+__device__ __forceinline__ void general_path(const TParams& P, float2 (*sh)[TB + 2][TB + 2]) {
     constexpr int W = TB - 2 * K;  // output columns per side
-    __shared__ float2 sh[2][TB][TB];
     const int tx = threadIdx.x, ty = threadIdx.y;
     const Layout& L = P.L;
     const bool periodic = P.bc == HG_BC_PERIODIC;
@@ -126,7 +125,7 @@ __global__ void __launch_bounds__(TB* TB, 1) k_temporal_f32k(const TParams P) {
             const float dprev = dq[t - 1][0];
             const int b = lvl & 1;
             ++lvl;
-            sh[b][ty][tx] = make_float2(c, lc);
+            sh[b][ty + 1][tx + 1] = make_float2(c, lc);
             __syncthreads();
             float oh = c, ol = lc, od = dprev;
             const bool in_win = tx >= t && tx < TB - t && ty >= t && ty < TB - t && pt >= z0 - (K - t) &&
@@ -135,8 +134,8 @@ __global__ void __launch_bounds__(TB* TB, 1) k_temporal_f32k(const TParams P) {
                 const bool zin = periodic || (pt >= 0 && pt < L.nz);
                 const bool zg = !periodic && (pt == -1 || pt == L.nz);
                 if (col_int && zin) {
-                    const float2 xl = sh[b][ty][tx - 1], xr = sh[b][ty][tx + 1];
-                    const float2 ys = sh[b][ty - 1][tx], yn = sh[b][ty + 1][tx];
+                    const float2 xl = sh[b][ty + 1][tx], xr = sh[b][ty + 1][tx + 2];
+                    const float2 ys = sh[b][ty][tx + 1], yn = sh[b][ty + 2][tx + 1];
                     f32k_update(xl.x, xr.x, ys.x, yn.x, qh[t - 1][0], qh[t - 1][2], c, xl.y, xr.y, ys.y, yn.y,
                                 ql[t - 1][0], ql[t - 1][2], lc, dprev, rq[t], P.nu2, oh, ol, od);
                 } else if (robin && ((col_int && zg) || ((col_fx || col_fy) && zin))) {
@@ -144,10 +143,10 @@ __global__ void __launch_bounds__(TB* TB, 1) k_temporal_f32k(const TParams P) {
                     float2 in;
                     long long row;
                     if (col_fx) {
-                        in = x < 0 ? sh[b][ty][tx + 1] : sh[b][ty][tx - 1];
+                        in = x < 0 ? sh[b][ty + 1][tx + 2] : sh[b][ty + 1][tx];
                         row = P.F.off[x < 0 ? 0 : 1] + (long long)pt * L.ny + y;
                     } else if (col_fy) {
-                        in = y < 0 ? sh[b][ty + 1][tx] : sh[b][ty - 1][tx];
+                        in = y < 0 ? sh[b][ty + 2][tx + 1] : sh[b][ty][tx + 1];
                         row = P.F.off[y < 0 ? 2 : 3] + (long long)pt * L.nx + x;
                     } else {
                         in = pt < 0 ? make_float2(qh[t - 1][2], ql[t - 1][2]) : make_float2(qh[t - 1][0], ql[t - 1][0]);
@@ -193,6 +192,126 @@ __global__ void __launch_bounds__(TB* TB, 1) k_temporal_f32k(const TParams P) {
             }
         }
     }
+}
+
+// Fast path for blocks whose whole 32 x 32 region lies inside the domain in x and y: no per-cell classification and
+// no shrinking-window tests -- every thread updates its column at every level (cells outside the valid trapezoid
+// compute values that are never written), only the z ghost planes need a (block-uniform) branch.
+template <int K>
+__device__ __forceinline__ void fast_path(const TParams& P, float2 (*sh)[TB + 2][TB + 2]) {
+    constexpr int W = TB - 2 * K;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const Layout& L = P.L;
+    const bool periodic = P.bc == HG_BC_PERIODIC;
+    const bool robin = P.bc == HG_BC_ROBIN;
+    const int x = -1 + (int)blockIdx.x * W + tx - K;
+    const int y = -1 + (int)blockIdx.y * W + ty - K;
+    const int z0 = -1 + (int)blockIdx.z * P.zchunk;
+    const int z1 = min(L.nz + 1, z0 + P.zchunk);
+    const bool out_col = tx >= K && tx < TB - K && ty >= K && ty < TB - K;
+    const long long col = L.at(x, y, -1) + L.plane;  // padded index of (x, y, 0)
+    const float* hi_c = P.hi_c + col;
+    const float* lo_c = P.lo_c + col;
+    const float* d_c = P.d_c + col;
+    const float* rs = P.rho + col;
+
+    float qh[K][3], ql[K][3], dq[K][2], rq[K + 1];
+#pragma unroll
+    for (int t = 0; t < K; ++t) {
+        qh[t][0] = qh[t][1] = qh[t][2] = 0.f;
+        ql[t][0] = ql[t][1] = ql[t][2] = 0.f;
+        dq[t][0] = dq[t][1] = 0.f;
+    }
+#pragma unroll
+    for (int t = 0; t <= K; ++t) rq[t] = 0.f;
+
+    auto load = [&](int p, float& h, float& l, float& d, float& r) {
+        int pw = p;
+        if (periodic) {
+            pw = wrap(p, L.nz);
+        } else if (p < -1 || p > L.nz) {
+            h = l = d = r = 0.f;
+            return;
+        }
+        const long long o = (long long)pw * L.plane;
+        h = __ldg(hi_c + o);
+        l = __ldg(lo_c + o);
+        d = __ldg(d_c + o);
+        r = __ldg(rs + o);
+    };
+
+    float nh, nl, nd, nr;
+    load(z0 - K, nh, nl, nd, nr);
+    int lvl = 0;
+    for (int p = z0 - K; p < z1 + K; ++p) {
+        const float h0 = nh, l0 = nl, d0 = nd, r0 = nr;
+        if (p + 1 < z1 + K) load(p + 1, nh, nl, nd, nr);
+        qh[0][0] = qh[0][1];
+        qh[0][1] = qh[0][2];
+        qh[0][2] = h0;
+        ql[0][0] = ql[0][1];
+        ql[0][1] = ql[0][2];
+        ql[0][2] = l0;
+        dq[0][0] = dq[0][1];
+        dq[0][1] = d0;
+#pragma unroll
+        for (int t = K; t > 0; --t) rq[t] = rq[t - 1];
+        rq[0] = r0;
+#pragma unroll
+        for (int t = 1; t <= K; ++t) {
+            const int pt = p - t;
+            const float c = qh[t - 1][1], lc = ql[t - 1][1];
+            const float dprev = dq[t - 1][0];
+            const int b = lvl & 1;
+            ++lvl;
+            sh[b][ty + 1][tx + 1] = make_float2(c, lc);
+            __syncthreads();
+            float oh = c, ol = lc, od = dprev;
+            if (periodic || (pt >= 0 && pt < L.nz)) {
+                const float2 xl = sh[b][ty + 1][tx], xr = sh[b][ty + 1][tx + 2];
+                const float2 ys = sh[b][ty][tx + 1], yn = sh[b][ty + 2][tx + 1];
+                f32k_update(xl.x, xr.x, ys.x, yn.x, qh[t - 1][0], qh[t - 1][2], c, xl.y, xr.y, ys.y, yn.y,
+                            ql[t - 1][0], ql[t - 1][2], lc, dprev, rq[t], P.nu2, oh, ol, od);
+            } else if (robin && (pt == -1 || pt == L.nz)) {
+                const float ih = pt < 0 ? qh[t - 1][2] : qh[t - 1][0], il = pt < 0 ? ql[t - 1][2] : ql[t - 1][0];
+                const float2 ab = P.robin32[P.F.off[pt < 0 ? 4 : 5] + (long long)y * L.nx + x];
+                robin_update_f32k(ab.x, ab.y, c, lc, ih, il, oh, ol);
+            }
+            if (t < K) {
+                qh[t][0] = qh[t][1];
+                qh[t][1] = qh[t][2];
+                qh[t][2] = oh;
+                ql[t][0] = ql[t][1];
+                ql[t][1] = ql[t][2];
+                ql[t][2] = ol;
+                dq[t][0] = dq[t][1];
+                dq[t][1] = od;
+            } else if (out_col && pt >= z0 && pt < z1) {
+                const long long q = col + (long long)pt * L.plane;
+                const bool zin = pt >= 0 && pt < L.nz;
+                if (zin) {
+                    P.hi_n[q] = oh;
+                    P.lo_n[q] = ol;
+                    P.d_n[q] = od;
+                } else if ((robin || periodic) && (pt == -1 || pt == L.nz)) {
+                    P.hi_n[q] = oh;  // Robin ghost update, or (periodic) the copy of the wrapped plane
+                    P.lo_n[q] = ol;
+                }
+            }
+        }
+    }
+}
+
+template <int K>
+__global__ void __launch_bounds__(TB* TB, 1) k_temporal_f32k(const TParams P) {
+    constexpr int W = TB - 2 * K;
+    __shared__ float2 sh[2][TB + 2][TB + 2];  // padded: edge threads of the fast path read (unused) padding
+    const int xr0 = -1 + (int)blockIdx.x * W - K, yr0 = -1 + (int)blockIdx.y * W - K;
+    const bool inside = xr0 >= 0 && xr0 + TB <= P.L.nx && yr0 >= 0 && yr0 + TB <= P.L.ny;
+    if (inside)
+        fast_path<K>(P, sh);
+    else
+        general_path<K>(P, sh);
 }
 
 template <int K>

@@ -1,6 +1,6 @@
 """Summarise an ncu launch list (--metrics gpu__time_duration.sum --csv) into per-kernel launches, time and share.
 
-usage: python profiles/summarize_launches.py launches.csv
+usage: python -m paper_1602_05700_gb300.ncu_summary launches.csv
 """
 import collections
 import csv

@@ -21,7 +21,7 @@ def _declared():
 
 @pytest.fixture(scope="module")
 def lib_path():
-    from paper_1602_05700_gb300.build import build
+    from paper_1602_05700_gb300.builder import build
     return build()
 
 
