@@ -204,6 +204,33 @@ int hg_batch_step(hg_batch* b, int n_substeps);
 int hg_batch_info(const hg_batch* b, int* z_planes_per_block, long long* blocks_per_substep);
 void hg_batch_free(hg_batch* b);
 
+/*
+ * The FP64 multipole moments Q_lm of a density, computed without allocating any GPU memory.
+ *
+ * The paper has no counterpart to this call; it exists for callers that are not allowed to call cudaMalloc: code
+ * whose device memory is owned and budgeted by someone else (a framework's caching allocator, a fixed-size pool
+ * shared by several solvers), or a loop that must not take the device-wide synchronisation a cudaMalloc or
+ * cudaFree can imply.  Such a caller cannot create a grid (hg_init_grid allocates its state), but can still get
+ * the boundary moments of its own density: it passes the input and the output, and the library supplies the
+ * scratch.
+ *
+ * rho: nz*ny*nx values of type dtype in device memory (C order, x fastest), cell (i,j,k) centred at
+ * origin + (i+1/2, j+1/2, k+1/2) h.  Q: (lmax+1)^2 doubles, in device memory (Q_on_device = 1) or host memory
+ * (Q_on_device = 0: the call then synchronises the stream); same definition and index as hg_get_moments.
+ * cuda_stream: the stream the work is enqueued on (NULL = legacy default stream), on the current device.
+ *
+ * Scratch: a fixed array compiled into the library, 304 x 81 + 81 doubles (197,640 bytes), present on every GPU
+ * that loads the library until the process exits.  Its size is what bounds lmax: lmax > HG_MAX_LMAX is rejected
+ * with HG_ERR_ARG; grid sizes are not limited by it.  The first call on each device looks up the array's device
+ * address (cudaGetSymbolAddress) with that device current and caches it; make that first call before any stream
+ * capture.  All calls on a device share the one array: every call overwrites the partial sums it uses, so no
+ * state carries over from the previous call, but calls whose GPU work overlaps in time (other streams, other host
+ * threads) race on the array and must be serialised by the caller.
+ * Errors: HG_ERR_ARG (null pointer, bad dtype, sizes < 1, h <= 0, lmax out of range), HG_ERR_CUDA.
+ */
+int hg_moments_noalloc(const void* rho, int dtype, int nx, int ny, int nz, double h, const double origin[3], int lmax,
+                       double* Q, int Q_on_device, void* cuda_stream);
+
 /* Message of the last failing call on this host thread ("" if none). */
 const char* hg_last_error(void);
 

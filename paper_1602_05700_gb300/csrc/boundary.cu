@@ -22,6 +22,8 @@
 // Condon-Shortley phase).
 #include <math.h>
 
+#include <mutex>
+
 #include "cell.cuh"
 #include "hg_internal.cuh"
 
@@ -337,3 +339,93 @@ int seed_ghosts(hg_grid* g) {
 }
 
 }  // namespace hg
+
+// ---- multipole moments without device allocation -------------------------------------------------------------
+// The paper has no counterpart to this: it is an entry point for callers that may not allocate GPU memory (see
+// hg_moments_noalloc in hg.h).  It runs the same moment and finishing kernels as hg_set_density, with the per-block
+// partial sums in a scratch array compiled into the library instead of in memory owned by a grid.
+namespace hg {
+namespace {
+
+// partial sums of kRedBlocks blocks for up to kMaxQ moments, then kMaxQ doubles for a result bound for host memory:
+// (304 * 81 + 81) doubles = 197,640 bytes on every GPU that loads the library, held until the process exits
+constexpr int kNoAllocDoubles = kRedBlocks * kMaxQ + kMaxQ;
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocDoubles];
+
+constexpr int kNoAllocDevices = 64;
+std::mutex g_noalloc_mu;
+double* g_noalloc_addr[kNoAllocDevices];  // device address of the scratch, per device, found on first use
+
+// The host name of g_noalloc_scratch is only a stand-in: the kernels need the device address, looked up once per
+// device (with that device current) and cached.
+int noalloc_scratch(double** out) {
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (dev < 0 || dev >= kNoAllocDevices) return fail(HG_ERR_ARG, "device index %d out of range", dev);
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        double* p = nullptr;
+        e = cudaGetSymbolAddress((void**)&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(moment scratch)");
+        g_noalloc_addr[dev] = p;
+    }
+    *out = g_noalloc_addr[dev];
+    return HG_OK;
+}
+
+template <int LMAX>
+int noalloc_moments(const void* rho, int dtype, int nx, int ny, int nz, double h, const double* o, double* scratch,
+                    double* Qdev, cudaStream_t st) {
+    constexpr int NQ = (LMAX + 1) * (LMAX + 1);
+    YlmNorm N;
+    fill_ylm_norms(N);
+    k_moments<LMAX><<<kRedBlocks, kRedThreads, 0, st>>>(rho, dtype, nx, ny, nz, h, o[0], o[1], o[2], N, scratch);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "multipole moment kernel");
+    k_finish<<<1, kRedThreads, 0, st>>>(scratch, kRedBlocks, NQ, Qdev);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "moment finish kernel");
+    return HG_OK;
+}
+
+}  // namespace
+}  // namespace hg
+
+extern "C" int hg_moments_noalloc(const void* rho, int dtype, int nx, int ny, int nz, double h, const double origin[3],
+                                  int lmax, double* Q, int Q_on_device, void* cuda_stream) {
+    using namespace hg;
+    if (!rho || !Q || !origin) return fail(HG_ERR_ARG, "null pointer");
+    if (dtype != HG_DT_F32 && dtype != HG_DT_F64) return fail(HG_ERR_ARG, "unknown dtype %d", dtype);
+    if (nx < 1 || ny < 1 || nz < 1) return fail(HG_ERR_ARG, "grid sizes must be >= 1 (got %d %d %d)", nx, ny, nz);
+    if (!(h > 0.0) || !isfinite(h) || !isfinite(origin[0]) || !isfinite(origin[1]) || !isfinite(origin[2]))
+        return fail(HG_ERR_ARG, "h must be positive and finite, origin finite");
+    if (lmax < 0 || lmax > HG_MAX_LMAX)
+        return fail(HG_ERR_ARG, "lmax = %d exceeds the fixed scratch of hg_moments_noalloc (sized for lmax <= %d)", lmax,
+                    HG_MAX_LMAX);
+    double* scratch = nullptr;
+    int rc = noalloc_scratch(&scratch);
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    double* Qdev = Q_on_device ? Q : scratch + (long long)kRedBlocks * kMaxQ;
+    switch (lmax) {
+        case 0: rc = noalloc_moments<0>(rho, dtype, nx, ny, nz, h, origin, scratch, Qdev, st); break;
+        case 1: rc = noalloc_moments<1>(rho, dtype, nx, ny, nz, h, origin, scratch, Qdev, st); break;
+        case 2: rc = noalloc_moments<2>(rho, dtype, nx, ny, nz, h, origin, scratch, Qdev, st); break;
+        case 3: rc = noalloc_moments<3>(rho, dtype, nx, ny, nz, h, origin, scratch, Qdev, st); break;
+        case 4: rc = noalloc_moments<4>(rho, dtype, nx, ny, nz, h, origin, scratch, Qdev, st); break;
+        case 5: rc = noalloc_moments<5>(rho, dtype, nx, ny, nz, h, origin, scratch, Qdev, st); break;
+        case 6: rc = noalloc_moments<6>(rho, dtype, nx, ny, nz, h, origin, scratch, Qdev, st); break;
+        case 7: rc = noalloc_moments<7>(rho, dtype, nx, ny, nz, h, origin, scratch, Qdev, st); break;
+        default: rc = noalloc_moments<8>(rho, dtype, nx, ny, nz, h, origin, scratch, Qdev, st); break;
+    }
+    if (rc) return rc;
+    if (!Q_on_device) {
+        const size_t bytes = (size_t)(lmax + 1) * (lmax + 1) * sizeof(double);
+        cudaError_t e = cudaMemcpyAsync(Q, Qdev, bytes, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return cuda_fail(e, "copy of the moments to host memory");
+    }
+    return HG_OK;
+}
+

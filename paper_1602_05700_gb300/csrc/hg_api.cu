@@ -38,7 +38,7 @@ int ensure_staging(hg_grid* g) {
     return HG_OK;
 }
 
-static void fill_ylm_norms(YlmNorm& N) {
+void fill_ylm_norms(YlmNorm& N) {
     const double pi = 3.14159265358979323846;
     for (int q = 0; q < kMaxQ; ++q) {
         N.n[q] = 0.0;

@@ -90,6 +90,7 @@ struct YlmNorm {
     double n[kMaxQ];        // normalisation of r^l Y_lm written as n_lm * q_l^m(z, r^2) * {C_m, S_m}
     double inv_lm[kMaxQ];   // 1 / (l - m) for the upward recurrence (index l*l + l + m, m >= 0)
 };
+void fill_ylm_norms(YlmNorm& N);
 
 // ---- the grid --------------------------------------------------------------------------------------------------
 }  // namespace hg
