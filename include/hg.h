@@ -115,6 +115,10 @@ int hg_step(hg_grid* g, int n_substeps);
 #define HG_MAX_TEMPORAL_DEPTH 4
 int hg_set_temporal_depth(hg_grid* g, int k);
 
+/* z planes per thread block of the single-sweep kernel (a tuning knob: more blocks and more z warm-up below, fewer
+ * and longer blocks above); 0 restores the built-in rule.  Results do not depend on it. */
+int hg_set_block_depth(hg_grid* g, int planes);
+
 /*
  * Gravitational acceleration a = -grad phi^n by second-order central differences, ghosts supplying the face
  * values.  ax, ay, az: device buffers of nz*ny*nx elements of type dtype.  Asynchronous.

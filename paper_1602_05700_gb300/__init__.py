@@ -121,6 +121,10 @@ class Grid:
     def set_temporal_depth(self, k):
         _lib.check(_lib.lib().hg_set_temporal_depth(self.handle, int(k)))
 
+    def set_block_depth(self, planes):
+        """z planes per block of the single-sweep kernel (0 = built-in rule); results do not depend on it."""
+        _lib.check(_lib.lib().hg_set_block_depth(self.handle, int(planes)))
+
     def accel(self, dtype=None, out=None):
         """-grad phi^n as three (nz, ny, nx) device tensors (written into `out` when given)."""
         torch = _torch()

@@ -1,8 +1,7 @@
 // Many independent grids advanced together (the batching workload: uneven sizes, mixed precisions).
 //
 // One sub-step of every grid is one batched kernel launch (stencil.cu, k_step_batch: block -> grid by a prefix
-// table, FP32-compensated and FP64 grids in the same launch), followed, if any grid is periodic, by one batched
-// ghost-copy launch.  hg_batch_step(b, n) records the n sub-steps once as a CUDA graph on the batch's own stream
+// table, FP32-compensated and FP64 grids in the same launch; boundary ghosts are written in the sweep's epilogue).  hg_batch_step(b, n) records the n sub-steps once as a CUDA graph on the batch's own stream
 // and replays it with a single graph launch; the kernels read the per-grid arguments from two device tables (for
 // the two time-level parities), refreshed from the grids before every replay, so the graph stays valid while the
 // grids' states move on.  Results are identical to stepping each grid on its own: the per-cell arithmetic is the
@@ -36,11 +35,6 @@ struct hg_batch {
     unsigned total_blocks;
     std::vector<unsigned> first;
     int zb;  // planes per block, 0 until tuned
-    // periodic copies
-    std::vector<int> periodic;  // indices of periodic grids
-    PeriodicArgs* d_ptab[2];
-    long long* d_pfirst;
-    long long ptotal;
     // graph of `graph_steps` sub-steps
     cudaGraph_t graph;
     cudaGraphExec_t exec;
@@ -70,7 +64,6 @@ std::string tune_key(const hg_batch* b) {
 // device tables for the sub-step that starts from parity p (0: every grid's current level, 1: the next one)
 int upload_tables(hg_batch* b) {
     std::vector<SweepArgs> tab[2];
-    std::vector<PeriodicArgs> ptab[2];
     for (int p = 0; p < 2; ++p) {
         for (hg_grid* g : b->grids) {
             const int cur = g->cur;
@@ -78,28 +71,13 @@ int upload_tables(hg_batch* b) {
             tab[p].push_back(sweep_args(g, b->zb));
             g->cur = cur;
         }
-        for (int i : b->periodic) {
-            hg_grid* g = b->grids[i];
-            const int nxt = (g->cur ^ p) ^ 1;  // the level the sweep of parity p writes
-            PeriodicArgs a;
-            a.prec = g->prec;
-            a.p = g->phi[nxt];
-            a.lo = g->lo[nxt];
-            a.L = g->L;
-            a.F = g->F;
-            ptab[p].push_back(a);
-        }
     }
     b->first.assign(1, 0);
     for (const SweepArgs& a : tab[0]) b->first.push_back(b->first.back() + sweep_blocks(a));
     b->total_blocks = b->first.back();
-    for (int p = 0; p < 2; ++p) {
+    for (int p = 0; p < 2; ++p)
         HG_CUDA(cudaMemcpyAsync(b->d_tab[p], tab[p].data(), tab[p].size() * sizeof(SweepArgs), cudaMemcpyHostToDevice,
                                 b->stream));
-        if (!b->periodic.empty())
-            HG_CUDA(cudaMemcpyAsync(b->d_ptab[p], ptab[p].data(), ptab[p].size() * sizeof(PeriodicArgs),
-                                    cudaMemcpyHostToDevice, b->stream));
-    }
     HG_CUDA(cudaMemcpyAsync(b->d_first, b->first.data(), b->first.size() * sizeof(unsigned), cudaMemcpyHostToDevice,
                             b->stream));
     HG_CUDA(cudaStreamSynchronize(b->stream));  // the host vectors go out of scope
@@ -107,13 +85,7 @@ int upload_tables(hg_batch* b) {
 }
 
 // the launches of one sub-step of parity p
-int enqueue_substep(hg_batch* b, int p) {
-    int rc = launch_step_batch(b->stream, b->d_tab[p], b->d_first, b->n, b->total_blocks);
-    if (rc) return rc;
-    if (!b->periodic.empty())
-        rc = launch_periodic_batch(b->stream, b->d_ptab[p], b->d_pfirst, (int)b->periodic.size(), b->ptotal);
-    return rc;
-}
+int enqueue_substep(hg_batch* b, int p) { return launch_step_batch(b->stream, b->d_tab[p], b->d_first, b->n, b->total_blocks); }
 
 void advance(hg_batch* b, int n) {
     for (hg_grid* g : b->grids) {
@@ -185,7 +157,7 @@ void destroy_graph(hg_batch* b) {
 
 void release(hg_batch* b) {
     destroy_graph(b);
-    void* ptrs[] = {b->d_tab[0], b->d_tab[1], b->d_first, b->d_ptab[0], b->d_ptab[1], b->d_pfirst};
+    void* ptrs[] = {b->d_tab[0], b->d_tab[1], b->d_first};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (b->ev_in) cudaEventDestroy(b->ev_in);
@@ -223,19 +195,6 @@ int hg_batch_create(hg_grid* const* grids, int n, hg_batch** out) {
     ck(cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming), "cudaEventCreate");
     for (int p = 0; p < 2 && rc == HG_OK; ++p) ck(cudaMalloc(&b->d_tab[p], n * sizeof(SweepArgs)), "cudaMalloc(table)");
     ck(cudaMalloc(&b->d_first, (n + 1) * sizeof(unsigned)), "cudaMalloc(table)");
-    std::vector<long long> pfirst(1, 0);
-    for (int i = 0; i < n; ++i)
-        if (grids[i]->bc == HG_BC_PERIODIC) {
-            b->periodic.push_back(i);
-            pfirst.push_back(pfirst.back() + grids[i]->F.off[6]);
-        }
-    b->ptotal = pfirst.back();
-    if (!b->periodic.empty() && rc == HG_OK) {
-        const size_t np = b->periodic.size();
-        for (int p = 0; p < 2; ++p) ck(cudaMalloc(&b->d_ptab[p], np * sizeof(PeriodicArgs)), "cudaMalloc(table)");
-        ck(cudaMalloc(&b->d_pfirst, (np + 1) * sizeof(long long)), "cudaMalloc(table)");
-        ck(cudaMemcpy(b->d_pfirst, pfirst.data(), (np + 1) * sizeof(long long), cudaMemcpyHostToDevice), "cudaMemcpy");
-    }
     if (rc == HG_OK) rc = upload_tables(b);
     if (rc != HG_OK) {
         release(b);

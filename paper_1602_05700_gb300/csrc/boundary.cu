@@ -8,11 +8,12 @@
 //                           time levels (rho, hence the data, is frozen during the sub-steps, Sec. 2).
 //   Robin                   monopole radiation condition d_t(r phi) + c_h d_r(r phi) = 0, d_r = d_n / mu,
 //                           mu = |x_g . n| / r_g, upwinded from the interior neighbour i:
-//                           phi_g^{n+1} = alpha phi_g^n + beta phi_i^n, alpha = 1 - nu/mu, beta = (nu/mu) r_i / r_g.
-//                           Its static limit r_g phi_g = r_i phi_i (gamma = r_i / r_g) seeds a new state.  The
+//                           u_g^{n+1} = u_g^n - (nu/mu)(u_g^n - u_i^n), u = r phi (FP64), or equivalently
+//                           phi_g^{n+1} = alpha phi_g^n + beta phi_i^n, alpha = 1 - nu/mu, beta = (nu/mu) r_i / r_g
+//                           (compensated float).  Its static limit r_g phi_g = r_i phi_i seeds a new state.  The
 //                           per-sub-step update is fused into the sweep kernels (stencil.cu, temporal.cu).
-//   Periodic                ghost = interior cell on the opposite face; the sweep kernels write these copies, the
-//                           kernel here fills them for a freshly seeded state.
+//   Periodic                ghost = interior cell on the opposite face; the sweep kernels write these copies (in their
+//                           epilogue), the kernel here fills them for a freshly seeded state or an adjoint injection.
 //
 // r^l Y_lm is evaluated as a polynomial (no trigonometry): with C_m + i S_m = (x + i y)^m,
 //   r^l Y_lm = n_lm q_l^m(z, r^2) {C_m (m > 0), 1 (m = 0), S_|m| (m < 0)},
@@ -185,14 +186,14 @@ __device__ __forceinline__ void write_phi(int prec, void* p, void* lo, long long
     }
 }
 
-// Robin static limit phi_g = gamma phi_i on one time level
+// Robin static limit r_g phi_g = r_i phi_i on one time level: phi_g = (phi_i r_i) / r_g
 __global__ void k_robin_static(int prec, void* p, void* lo, Layout L, Faces F, const double* __restrict__ coef) {
     long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (t >= F.off[6]) return;
     int gc[3], ic[3];
     face_cell(F, L.nx, L.ny, L.nz, t, gc, ic);
     const long long qg = L.at(gc[0], gc[1], gc[2]), qi = L.at(ic[0], ic[1], ic[2]);
-    write_phi(prec, p, lo, qg, __dmul_rn(coef[3 * t + 2], read_phi(prec, p, lo, qi)));
+    write_phi(prec, p, lo, qg, __ddiv_rn(__dmul_rn(read_phi(prec, p, lo, qi), coef[3 * t + 2]), coef[3 * t + 1]));
 }
 
 // periodic copy into the face ghosts of one time level
@@ -215,23 +216,6 @@ __global__ void k_periodic(int prec, void* p, void* lo, Layout L, Faces F) {
     long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (t >= F.off[6]) return;
     periodic_ghost(prec, p, lo, L, F, t);
-}
-
-// periodic copies for several grids in one launch: ghost t of the concatenation belongs to the entry e with
-// first[e] <= t < first[e+1]
-__global__ void k_periodic_batch(const PeriodicArgs* __restrict__ tab, const long long* __restrict__ first, int n) {
-    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (t >= first[n]) return;
-    int lo = 0, hi = n - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (first[mid] <= t)
-            lo = mid;
-        else
-            hi = mid - 1;
-    }
-    const PeriodicArgs& A = tab[lo];
-    periodic_ghost(A.prec, A.p, A.lo, A.L, A.F, t - first[lo]);
 }
 
 template <int LMAX>
@@ -298,23 +282,13 @@ int set_ghosts_dirichlet(hg_grid* g) {
     }
 }
 
-// periodic copies into the face ghosts of time-level buffer b (1 - cur: the level a single sweep just wrote)
+// periodic copies into the face ghosts of time-level buffer b
 int launch_periodic_fill(hg_grid* g, int b) {
     long long n = g->F.off[6];
     int threads = 256;
     unsigned blocks = (unsigned)((n + threads - 1) / threads);
     k_periodic<<<blocks, threads, 0, g->stream>>>(g->prec, g->phi[b], g->lo[b], g->L, g->F);
     HG_LAUNCHED("periodic ghost kernel");
-    return HG_OK;
-}
-
-int launch_periodic_copy(hg_grid* g) { return launch_periodic_fill(g, 1 - g->cur); }
-
-int launch_periodic_batch(cudaStream_t st, const PeriodicArgs* tab, const long long* first, int n, long long total) {
-    if (total <= 0) return HG_OK;
-    k_periodic_batch<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(tab, first, n);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_fail(e, "batched periodic ghost kernel");
     return HG_OK;
 }
 

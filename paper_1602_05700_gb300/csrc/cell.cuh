@@ -35,24 +35,30 @@ __device__ __forceinline__ void f32k_update(float xl, float xr, float ys, float 
     d_o = dn;
 }
 
-// f64: phi^{n+1} = c + ((c - prev) + fma(nu2, L, -s)), L = ((xl-c) + (xr-c)) + ((ys-c) + (yn-c)) + ((zm-c) + (zp-c)):
-// 15 FP64 instructions per cell
+// f64: phi^{n+1} = ((2c - prev) + nu^2 L) - s with L = (((((xl-c) + (xr-c)) + (ys-c)) + (yn-c)) + (zm-c)) + (zp-c):
+// each operation rounded separately, in this order -- the plain evaluation of the update, 16 FP64 instructions.
+// Every FP64 rounding of the step is thereby fixed by the formula alone, so any IEEE implementation that evaluates
+// it in the same order without contraction produces the same bits.
 __device__ __forceinline__ double f64_update(double xl, double xr, double ys, double yn, double zm, double zp, double c,
                                              double prev, double s, double nu2) {
-    const double Lx = __dadd_rn(__dsub_rn(xl, c), __dsub_rn(xr, c));
-    const double Ly = __dadd_rn(__dsub_rn(ys, c), __dsub_rn(yn, c));
-    const double Lz = __dadd_rn(__dsub_rn(zm, c), __dsub_rn(zp, c));
-    const double L = __dadd_rn(__dadd_rn(Lx, Ly), Lz);
-    return __dadd_rn(c, __dadd_rn(__dsub_rn(c, prev), __fma_rn(nu2, L, -s)));
+    double L = __dadd_rn(__dsub_rn(xl, c), __dsub_rn(xr, c));
+    L = __dadd_rn(L, __dsub_rn(ys, c));
+    L = __dadd_rn(L, __dsub_rn(yn, c));
+    L = __dadd_rn(L, __dsub_rn(zm, c));
+    L = __dadd_rn(L, __dsub_rn(zp, c));
+    return __dsub_rn(__dadd_rn(__dsub_rn(__dmul_rn(2.0, c), prev), __dmul_rn(nu2, L)), s);
 }
 
-// Robin ghost sub-step (monopole radiation condition, upwinded): phi_g' = alpha phi_g + beta phi_i, in FP64
-__device__ __forceinline__ double robin_update(double alpha, double beta, double phi_g, double phi_i) {
-    return __fma_rn(alpha, phi_g, __dmul_rn(beta, phi_i));
+// Robin ghost sub-step in FP64 (monopole radiation condition, upwinded) for u = r phi:
+// u_g' = u_g - a (u_g - u_i), phi_g' = u_g' / r_g, with a = nu / mu, in that order of operations
+__device__ __forceinline__ double robin_update_f64(double a, double rg, double ri, double phi_g, double phi_i) {
+    const double ug = __dmul_rn(rg, phi_g), ui = __dmul_rn(ri, phi_i);
+    return __ddiv_rn(__dsub_rn(ug, __dmul_rn(a, __dsub_rn(ug, ui))), rg);
 }
 
-// The same update for the compensated float state, without FP64 (GB300's FP64 and its f32<->f64 conversions are
-// slow): alpha, beta rounded to float; both products and their sum carried as float pairs by error-free
+// The same update for the compensated float state, written phi_g' = alpha phi_g + beta phi_i (alpha = 1 - a,
+// beta = a r_i / r_g), without FP64 (GB300's FP64 and its f32<->f64 conversions are slow): alpha, beta rounded to
+// float; both products and their sum carried as float pairs by error-free
 // transformations (TwoProduct with an FMA, TwoSum), the compensations added, then one Fast2Sum.
 __device__ __forceinline__ void robin_update_f32k(float a, float b, float hg, float lg, float hin, float lin,
                                                   float& hi_o, float& lo_o) {

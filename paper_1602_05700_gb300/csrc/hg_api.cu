@@ -56,7 +56,8 @@ void fill_ylm_norms(YlmNorm& N) {
 
 static int dt_size(int dtype) { return dtype == HG_DT_F64 ? 8 : 4; }
 
-// Robin coefficients (alpha, beta, gamma) of every face ghost; rejects nu/mu > 1 (unstable upwind update)
+// Robin coefficients of every face ghost: a = nu/mu and the radii r_g, r_i (FP64 grids), alpha = 1 - a and
+// beta = a r_i/r_g in float (compensated float grids); rejects nu/mu > 1 (unstable upwind update)
 static int build_robin(hg_grid* g) {
     long long n = g->F.off[6];
     std::vector<double> c((size_t)(3 * n));
@@ -75,18 +76,19 @@ static int build_robin(hg_grid* g) {
         if (!(rg > 0.0) || !(along > 0.0))
             return fail(HG_ERR_CFL, "Robin boundary: ghost (%d,%d,%d) does not face away from the origin; the domain must "
                                     "surround the coordinate origin", gc[0], gc[1], gc[2]);
-        double a = g->nu / (along / rg);
+        double a = g->nu / (fabs(along) / rg);
         if (a > worst) worst = a;
-        c[3 * t] = 1.0 - a;
-        c[3 * t + 1] = a * ri / rg;
-        c[3 * t + 2] = ri / rg;
+        c[3 * t] = a;
+        c[3 * t + 1] = rg;
+        c[3 * t + 2] = ri;
     }
     if (worst > 1.0 + 1e-12)
         return fail(HG_ERR_CFL, "Robin boundary: nu/mu = %.6f > 1 at some ghost (reduce dt or centre the domain)", worst);
     HG_CUDA(cudaMalloc(&g->robin, c.size() * sizeof(double)));
     HG_CUDA(cudaMemcpy(g->robin, c.data(), c.size() * sizeof(double), cudaMemcpyHostToDevice));
-    std::vector<float2> c32((size_t)n);
-    for (long long t = 0; t < n; ++t) c32[t] = make_float2((float)c[3 * t], (float)c[3 * t + 1]);
+    std::vector<float2> c32((size_t)n);  // alpha = 1 - a, beta = a r_i / r_g
+    for (long long t = 0; t < n; ++t)
+        c32[t] = make_float2((float)(1.0 - c[3 * t]), (float)(c[3 * t] * c[3 * t + 2] / c[3 * t + 1]));
     HG_CUDA(cudaMalloc(&g->robin32, c32.size() * sizeof(float2)));
     HG_CUDA(cudaMemcpy(g->robin32, c32.data(), c32.size() * sizeof(float2), cudaMemcpyHostToDevice));
     return HG_OK;
@@ -314,6 +316,14 @@ int hg_set_temporal_depth(hg_grid* g, int k) {
     return HG_OK;
 }
 
+int hg_set_block_depth(hg_grid* g, int planes) {
+    int rc = check_grid(g);
+    if (rc) return rc;
+    if (planes < 0) return fail(HG_ERR_ARG, "planes must be >= 0");
+    g->zb = planes;
+    return HG_OK;
+}
+
 int hg_step(hg_grid* g, int n_substeps) {
     int rc = check_grid(g);
     if (rc) return rc;
@@ -321,12 +331,11 @@ int hg_step(hg_grid* g, int n_substeps) {
     int s = 0;
     while (s < n_substeps) {
         int k = n_substeps - s < g->tdepth ? n_substeps - s : g->tdepth;
-        // the sweep launches also write the Robin ghosts of the new level; the fused kernel the periodic ones too
+        // the sweep launches also write the face ghosts of the new level (Robin update, periodic copy)
         if (k >= 2) {
             if ((rc = launch_temporal(g, k))) return rc;
         } else {
             if ((rc = launch_step_single(g))) return rc;
-            if (g->bc == HG_BC_PERIODIC && (rc = launch_periodic_copy(g))) return rc;
         }
         g->cur = 1 - g->cur;
         if (k >= 2) g->dcur = 1 - g->dcur;
@@ -563,7 +572,6 @@ int hg_adjoint_step(hg_grid* g, int n_substeps) {
     for (int s = 0; s < n_substeps; ++s) {
         if ((rc = adjoint_accumulate(a, g->acc[0], g->acc[1]))) return rc;
         if ((rc = launch_step_single(a))) return rc;
-        if (a->bc == HG_BC_PERIODIC && (rc = launch_periodic_copy(a))) return rc;
         a->cur = 1 - a->cur;
         ++a->step;
     }

@@ -116,7 +116,7 @@ struct hg_grid {
     int dcur;
     void* rho;  // stored source s = (c dt)^2 4 pi G (rho - rho_bar), rho_bar = mean(rho) for periodic boundaries, else 0
     int cur;
-    double* robin;  // 3 doubles per face ghost: alpha, beta, gamma (see boundary.cu)
+    double* robin;  // 3 doubles per face ghost: a = nu/mu, r_g, r_i (see boundary.cu)
     float2* robin32;  // alpha, beta rounded to float (compensated float grids)
     double* red;    // reduction scratch
     long long red_elems;
@@ -165,7 +165,6 @@ int launch_step_single(hg_grid* g);                  // one interior sweep: cur 
 int adjoint_inject(hg_grid* a, const void* v, int vdt);
 int adjoint_accumulate(hg_grid* a, void* acc_a, void* acc_b);
 int adjoint_gradient(hg_grid* a, const void* acc_a, const void* acc_b, void* out, int odt, double* scratch);
-int launch_periodic_copy(hg_grid* g);                // periodic ghosts of the new level after a single sweep
 int launch_periodic_fill(hg_grid* g, int b);         // periodic ghosts of time-level buffer b
 int launch_temporal(hg_grid* g, int k);              // k fused sub-steps: cur -> 1-cur (temporal.cu)
 int ensure_staging(hg_grid* g);
@@ -187,9 +186,11 @@ int prof_fold(hg_grid* g);   // synchronise and add the recorded pairs to prof_m
 
 // ---- sweep arguments (stencil.cu) ----
 struct Bnd {
-    int faces;              // 1: Robin ghosts to update
+    int faces;              // 1: Robin ghosts to update (block epilogue)
+    int periodic;           // 1: copy the new boundary cells into the opposite ghosts (block epilogue)
+    int xfaces;             // 0, or HG_BC_ROBIN / HG_BC_PERIODIC: the x-face ghosts are produced inside the sweep loop
     const float2* robin32;  // (alpha, beta) per face ghost, compensated float grids
-    const double* robin;    // (alpha, beta, gamma) per face ghost, FP64 grids
+    const double* robin;    // (a = nu/mu, r_g, r_i) per face ghost, FP64 grids
     long long off[7];       // face offsets in the ghost enumeration (hg::Faces)
 };
 
@@ -203,21 +204,12 @@ struct SweepArgs {
     const void* rho;   // scaled source s
     Layout L;
     double nu2;
+    float nu2f;        // nu^2 rounded to float once (compensated float sweeps)
     int zb;            // z planes per block
     int prec;
     unsigned gx, gy;   // blocks in x and y of this grid's sweep
     Bnd B;
 };
-
-// periodic ghost copies of one time level of one grid (an entry of a batched copy)
-struct PeriodicArgs {
-    int prec;
-    void* p;
-    void* lo;
-    Layout L;
-    Faces F;
-};
-int launch_periodic_batch(cudaStream_t st, const PeriodicArgs* tab, const long long* first, int n, long long total);
 
 SweepArgs sweep_args(const hg_grid* g, int zb);  // sub-step cur -> 1 - cur of grid g; zb = 0: default z chunk
 unsigned sweep_blocks(const SweepArgs& A);

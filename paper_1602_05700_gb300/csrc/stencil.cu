@@ -38,12 +38,11 @@ __device__ __forceinline__ void set(float4& v, int e, float x) {
     if (e == 0) v.x = x; else if (e == 1) v.y = x; else if (e == 2) v.z = x; else v.w = x;
 }
 
-// Robin boundary work rides in the same launch, after each block's z-march (so it adds no registers to the sweep):
+// Boundary work rides in the same launch, after each block's z-march (so it adds no registers to the sweep).  Robin:
 // a block next to a face updates the face ghosts that border its own cells -- its rows and planes of an x face, its
 // x range and planes of a y face, its x range and rows of a z face -- to level n+1, from level-n values only (the
 // ghost and its interior neighbour), which no block of the launch writes.  Every face ghost belongs to exactly one
-// block.  Dirichlet ghosts are data; periodic copies of the new level are made by a small kernel after the sweep
-// (boundary.cu).
+// block.  Dirichlet ghosts are data.  Periodic: see block_periodic_copies.
 
 
 
@@ -110,6 +109,47 @@ __device__ __forceinline__ void block_face_ghosts(const Layout& L, const Bnd& B,
         }, upd);
 }
 
+// Periodic boundaries: after its own sweep (and a block barrier, so that the block sees what its threads wrote),
+// a block copies the new values of its cells on a face into the ghosts of the opposite face.  copy(src, dst) takes
+// padded indices; each boundary cell belongs to exactly one block.
+template <class Copy>
+__device__ __forceinline__ void block_periodic_copies(const Layout& L, int x0, int j0, int wy, int k0, int k1, int bx,
+                                                      int by, int gx, int gy, Copy&& copy) {
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x, nth = blockDim.x * blockDim.y;
+    const int jn = min(wy, L.ny - j0), xn = min(128, L.nx - x0), kn = k1 - k0;
+    const long long wx = L.nx, wy_ = (long long)L.ny * L.pitch, wz = (long long)L.nz * L.plane;
+    if (bx == 0)
+        for (int t = tid; t < jn * kn; t += nth) {
+            const long long q = L.at(0, j0 + t % jn, k0 + t / jn);
+            copy(q, q + wx);
+        }
+    if (bx == gx - 1)
+        for (int t = tid; t < jn * kn; t += nth) {
+            const long long q = L.at(L.nx - 1, j0 + t % jn, k0 + t / jn);
+            copy(q, q - wx);
+        }
+    if (by == 0)
+        for (int t = tid; t < xn * kn; t += nth) {
+            const long long q = L.at(x0 + t % xn, 0, k0 + t / xn);
+            copy(q, q + wy_);
+        }
+    if (by == gy - 1)
+        for (int t = tid; t < xn * kn; t += nth) {
+            const long long q = L.at(x0 + t % xn, L.ny - 1, k0 + t / xn);
+            copy(q, q - wy_);
+        }
+    if (k0 == 0)
+        for (int t = tid; t < xn * jn; t += nth) {
+            const long long q = L.at(x0 + t % xn, j0 + t / xn, 0);
+            copy(q, q + wz);
+        }
+    if (k1 == L.nz)
+        for (int t = tid; t < xn * jn; t += nth) {
+            const long long q = L.at(x0 + t % xn, j0 + t / xn, L.nz - 1);
+            copy(q, q - wz);
+        }
+}
+
 template <int WY>
 __device__ __forceinline__ void sweep_f32k(const SweepArgs& A, int bx, int by, int bz) {
     const float* __restrict__ hi_c = (const float*)A.hi_c;
@@ -120,7 +160,7 @@ __device__ __forceinline__ void sweep_f32k(const SweepArgs& A, int bx, int by, i
     const float* __restrict__ rho = (const float*)A.rho;
     const Layout& L = A.L;
     const Bnd& B = A.B;
-    const float nu2 = (float)A.nu2;
+    const float nu2 = A.nu2f;
     const int zb = A.zb;
     const int lane = threadIdx.x;
     const int j = by * WY + threadIdx.y;
@@ -201,6 +241,37 @@ __device__ __forceinline__ void sweep_f32k(const SweepArgs& A, int bx, int by, i
                         dlt[q + e] = el(dout, e);
                     }
             }
+            // x-face ghosts of level n+1, by the two lanes that hold the face cells (the ghosts lie one element away
+            // in the same rows, so these stores are the only scattered ones, and they overlap the stream)
+            if (B.xfaces) {
+                const int elast = L.nx - 1 - i0;  // element holding cell nx-1, if 0..3
+                if (B.xfaces == HG_BC_ROBIN) {
+                    if (i0 == 0) {
+                        const float2 ab = B.robin32[B.off[0] + (long long)k * L.ny + j];
+                        float gh, gl;
+                        robin_update_f32k(ab.x, ab.y, hl, ll, hc.x, lc.x, gh, gl);
+                        hi_n[q - 1] = gh;
+                        lo_n[q - 1] = gl;
+                    }
+                    if (elast >= 0 && elast < 4) {
+                        const float2 ab = B.robin32[B.off[1] + (long long)k * L.ny + j];
+                        const float xg = elast == 3 ? hr : el(hc, elast + 1), lg = elast == 3 ? lr : el(lc, elast + 1);
+                        float gh, gl;
+                        robin_update_f32k(ab.x, ab.y, xg, lg, el(hc, elast), el(lc, elast), gh, gl);
+                        hi_n[q + elast + 1] = gh;
+                        lo_n[q + elast + 1] = gl;
+                    }
+                } else {  // periodic: cell 0 -> ghost nx, cell nx-1 -> ghost -1
+                    if (i0 == 0) {
+                        hi_n[q + L.nx] = ho.x;
+                        lo_n[q + L.nx] = lo.x;
+                    }
+                    if (elast >= 0 && elast < 4) {
+                        hi_n[q + elast - L.nx] = el(ho, elast);
+                        lo_n[q + elast - L.nx] = el(lo, elast);
+                    }
+                }
+            }
         }
         hm = hc;
         hc = hp;
@@ -230,6 +301,13 @@ __device__ __forceinline__ void sweep_f32k(const SweepArgs& A, int bx, int by, i
                     lo_n[gb.qg[u]] = gl;
                 }
         });
+    if (B.periodic) {
+        __syncthreads();
+        block_periodic_copies(L, bx * 128, by * WY, WY, k0, k1, bx, by, A.gx, A.gy, [&](long long q, long long d) {
+            hi_n[d] = hi_n[q];
+            lo_n[d] = lo_n[q];
+        });
+    }
 }
 
 // f64: 4 cells per lane as two double2 (arithmetic in cell.cuh)
@@ -321,27 +399,97 @@ __device__ __forceinline__ void sweep_f64(const SweepArgs& A, int bx, int by, in
     }
     if (B.faces)
         block_face_ghosts(L, B, bx * 128, by * WY, WY, k0, k1, bx, by, A.gx, A.gy, [&](const GhostBatch& gb) {
-            double a[kGB], b[kGB], pg[kGB], pi[kGB];
+            double a[kGB], rg[kGB], ri[kGB], pg[kGB], pi[kGB];
 #pragma unroll
             for (int u = 0; u < kGB; ++u)
                 if (u < gb.n) {
                     a[u] = B.robin[3 * gb.t[u]];
-                    b[u] = B.robin[3 * gb.t[u] + 1];
+                    rg[u] = B.robin[3 * gb.t[u] + 1];
+                    ri[u] = B.robin[3 * gb.t[u] + 2];
                     pg[u] = __ldg(phi_c + gb.qg[u]);
                     pi[u] = __ldg(phi_c + gb.qi[u]);
                 }
 #pragma unroll
             for (int u = 0; u < kGB; ++u)
-                if (u < gb.n) phi_pn[gb.qg[u]] = robin_update(a[u], b[u], pg[u], pi[u]);
+                if (u < gb.n) phi_pn[gb.qg[u]] = robin_update_f64(a[u], rg[u], ri[u], pg[u], pi[u]);
         });
+    if (B.periodic) {
+        __syncthreads();
+        block_periodic_copies(L, bx * 128, by * WY, WY, k0, k1, bx, by, A.gx, A.gy,
+                              [&](long long q, long long d) { phi_pn[d] = phi_pn[q]; });
+    }
 }
 
 constexpr int kWY = 8;
 
+// ---- boundary kernels of a single-grid sub-step (one thread per face ghost) ----
+// ghost t of the face-major enumeration -> padded indices of the ghost, of its interior neighbour, and of the
+// interior cell on the opposite face (the periodic source); 32-bit in-face arithmetic
+__device__ __forceinline__ void ghost_cells(const Layout& L, const Bnd& B, int t, long long& qg, long long& qi,
+                                            long long& qo) {
+    int f = 0, base = 0;
+#pragma unroll
+    for (int u = 1; u < 6; ++u)
+        if (t >= (int)B.off[u]) {
+            f = u;
+            base = (int)B.off[u];
+        }
+    const int r = t - base;
+    const int na = f < 2 ? L.ny : L.nx;
+    const int a = r % na, b = r / na;
+    switch (f) {
+        case 0: qg = L.at(-1, a, b); qi = qg + 1; qo = L.at(L.nx - 1, a, b); break;
+        case 1: qg = L.at(L.nx, a, b); qi = qg - 1; qo = L.at(0, a, b); break;
+        case 2: qg = L.at(a, -1, b); qi = qg + L.pitch; qo = L.at(a, L.ny - 1, b); break;
+        case 3: qg = L.at(a, L.ny, b); qi = qg - L.pitch; qo = L.at(a, 0, b); break;
+        case 4: qg = L.at(a, b, -1); qi = qg + L.plane; qo = L.at(a, b, L.nz - 1); break;
+        default: qg = L.at(a, b, L.nz); qi = qg - L.plane; qo = L.at(a, b, 0); break;
+    }
+}
+
+// Robin: ghosts of level n+1 from level n (runs before the sweep; the sweep neither reads nor writes them).  The
+// x faces (whose ghosts are strided in memory) are done by the compensated-float sweep itself, so for those grids
+// this kernel covers the y and z faces only (t0 = first y-face ghost).
+__global__ void __launch_bounds__(256) k_ghosts_robin(const SweepArgs A, int t0) {
+    const int t = t0 + blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int)A.B.off[6]) return;
+    long long qg, qi, qo;
+    ghost_cells(A.L, A.B, t, qg, qi, qo);
+    if (A.prec == HG_PREC_F32K) {
+        const float* hc = (const float*)A.hi_c;
+        const float* lc = (const float*)A.lo_c;
+        const float2 ab = A.B.robin32[t];
+        float gh, gl;
+        robin_update_f32k(ab.x, ab.y, __ldg(hc + qg), __ldg(lc + qg), __ldg(hc + qi), __ldg(lc + qi), gh, gl);
+        ((float*)A.hi_n)[qg] = gh;
+        ((float*)A.lo_n)[qg] = gl;
+    } else {
+        const double* pc = (const double*)A.hi_c;
+        const double* R = A.B.robin;
+        ((double*)A.hi_n)[qg] = robin_update_f64(R[3 * t], R[3 * t + 1], R[3 * t + 2], __ldg(pc + qg), __ldg(pc + qi));
+    }
+}
+
+// periodic: ghosts of level n+1 are copies of the new values on the opposite face (runs after the sweep)
+__global__ void __launch_bounds__(256) k_ghosts_periodic(const SweepArgs A, int t0) {
+    const int t = t0 + blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int)A.B.off[6]) return;
+    long long qg, qi, qo;
+    ghost_cells(A.L, A.B, t, qg, qi, qo);
+    if (A.prec == HG_PREC_F32K) {
+        ((float*)A.hi_n)[qg] = ((const float*)A.hi_n)[qo];
+        ((float*)A.lo_n)[qg] = ((const float*)A.lo_n)[qo];
+    } else {
+        ((double*)A.hi_n)[qg] = ((const double*)A.hi_n)[qo];
+    }
+}
+
 int zchunk(const hg_grid* g) {
-    // enough blocks for several waves on 152 SMs without making the z warm-up (2 planes) a large fraction
+    // enough blocks for several waves on 152 SMs without making the z warm-up (2 planes) a large fraction; Robin
+    // grids want about twice as many blocks (the blocks at the x faces also update the face ghosts, and finer
+    // blocks balance that extra work better: measured 0.630 against 0.651 ms per sub-step at 512^3)
     long long xy = (long long)((g->nx + 127) / 128) * ((g->ny + kWY - 1) / kWY);
-    long long want = 152LL * 8 * 3;
+    long long want = 152LL * 8 * (g->bc == HG_BC_ROBIN ? 6 : 3);
     long long nzb = (want + xy - 1) / xy;
     if (nzb < 1) nzb = 1;
     int zb = (int)((g->nz + nzb - 1) / nzb);
@@ -356,7 +504,7 @@ __global__ void __launch_bounds__(32 * WY, 3) k_step_f32k(const SweepArgs A) {
 }
 
 template <int WY>
-__global__ void __launch_bounds__(32 * WY, 3) k_step_f64(const SweepArgs A) {
+__global__ void __launch_bounds__(32 * WY, 2) k_step_f64(const SweepArgs A) {
     sweep_f64<WY>(A, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
@@ -364,7 +512,7 @@ __global__ void __launch_bounds__(32 * WY, 3) k_step_f64(const SweepArgs A) {
 // (binary search in the prefix table), and runs that grid's sweep body for its local block coordinates.  Grids of
 // both precisions mix in one launch (the branch is uniform per block).
 template <int WY>
-__global__ void __launch_bounds__(32 * WY, 3) k_step_batch(const SweepArgs* __restrict__ tab,
+__global__ void __launch_bounds__(32 * WY, 2) k_step_batch(const SweepArgs* __restrict__ tab,
                                                            const unsigned* __restrict__ first, int n) {
     const unsigned b = blockIdx.x;
     int lo = 0, hi = n - 1;
@@ -398,11 +546,14 @@ SweepArgs sweep_args(const hg_grid* g, int zb) {
     A.rho = g->rho;
     A.L = g->L;
     A.nu2 = g->nu2;
+    A.nu2f = (float)g->nu2;
     A.zb = zb > 0 ? (zb < g->nz ? zb : g->nz) : zchunk(g);
     A.prec = g->prec;
     A.gx = (g->nx + 127) / 128;
     A.gy = (g->ny + kWY - 1) / kWY;
     A.B.faces = g->bc == HG_BC_ROBIN ? 1 : 0;
+    A.B.periodic = g->bc == HG_BC_PERIODIC ? 1 : 0;
+    A.B.xfaces = 0;
     A.B.robin32 = g->robin32;
     A.B.robin = g->robin;
     for (int f = 0; f < 7; ++f) A.B.off[f] = g->F.off[f];
@@ -411,10 +562,23 @@ SweepArgs sweep_args(const hg_grid* g, int zb) {
 
 unsigned sweep_blocks(const SweepArgs& A) { return A.gx * A.gy * (unsigned)((A.L.nz + A.zb - 1) / A.zb); }
 
+// A single grid's sub-step: [Robin ghost kernel] -> sweep -> [periodic ghost kernel].  The boundary work runs as
+// its own small launches here (measured cheaper than the sweep epilogue, which lengthens the boundary blocks); the
+// batched launch keeps the epilogue form.
 int launch_step_single(hg_grid* g) {
-    const SweepArgs A = sweep_args(g, g->zb);
+    SweepArgs A = sweep_args(g, g->zb);
+    const int robin = A.B.faces, periodic = A.B.periodic;
+    A.B.faces = 0;
+    A.B.periodic = 0;
+    if (g->prec == HG_PREC_F32K && (robin || periodic)) A.B.xfaces = g->bc;
+    const int t0 = A.B.xfaces ? (int)A.B.off[2] : 0;  // ghosts left to the separate kernels
     dim3 block(32, kWY);
     dim3 grid(A.gx, A.gy, (g->nz + A.zb - 1) / A.zb);
+    const unsigned gblocks = (unsigned)((A.B.off[6] - t0 + 255) / 256);
+    if (robin) {
+        k_ghosts_robin<<<gblocks, 256, 0, g->stream>>>(A, t0);
+        HG_LAUNCHED("Robin ghost kernel");
+    }
     int rc = prof_begin(g);
     if (rc) return rc;
     if (g->prec == HG_PREC_F32K)
@@ -422,7 +586,12 @@ int launch_step_single(hg_grid* g) {
     else
         k_step_f64<kWY><<<grid, block, 0, g->stream>>>(A);
     HG_LAUNCHED("stencil sub-step kernel");
-    return prof_end(g);
+    if ((rc = prof_end(g))) return rc;
+    if (periodic) {
+        k_ghosts_periodic<<<gblocks, 256, 0, g->stream>>>(A, t0);
+        HG_LAUNCHED("periodic ghost kernel");
+    }
+    return HG_OK;
 }
 
 int launch_step_batch(cudaStream_t st, const SweepArgs* tab, const unsigned* first, int n, unsigned total_blocks) {

@@ -49,9 +49,15 @@ __device__ __forceinline__ int wrap(int v, int n) {
     return v < 0 ? v + n : v;
 }
 
-template <int K>
-__device__ __forceinline__ void general_path(const TParams& P, float2 (*sh)[TB + 2][TB + 2]) {
-    constexpr int W = TB - 2 * K;  // output columns per side
+// One code path for every block.  EDGE = false is used when the block's whole 32 x 32 region lies inside the domain
+// in x and y: no per-cell classification at all.  EDGE = true classifies each column once (interior, x-face ghost,
+// y-face ghost, or outside) and each plane per level (interior or ghost plane, uniform over the block); ghost cells
+// follow their boundary condition, cells outside the domain keep whatever they hold.  No cell tests whether it lies
+// in the shrinking valid window: cells near the region edge compute values from unused padding, and those values
+// never reach the written inner 32 - 2K columns (each level's valid region shrinks by one cell per side).
+template <int K, bool EDGE>
+__device__ __forceinline__ void region_sweep(const TParams& P, float2 (*sh)[TB + 2][TB + 2]) {
+    constexpr int W = TB - 2 * K;
     const int tx = threadIdx.x, ty = threadIdx.y;
     const Layout& L = P.L;
     const bool periodic = P.bc == HG_BC_PERIODIC;
@@ -61,155 +67,24 @@ __device__ __forceinline__ void general_path(const TParams& P, float2 (*sh)[TB +
     const int z0 = -1 + (int)blockIdx.z * P.zchunk;
     const int z1 = min(L.nz + 1, z0 + P.zchunk);  // output planes [z0, z1)
 
-    // column classification (non-periodic): interior, x-face ghost, y-face ghost, or dead
-    const bool xin = x >= 0 && x < L.nx, yin = y >= 0 && y < L.ny;
-    const bool xg = x == -1 || x == L.nx, yg = y == -1 || y == L.ny;
-    const bool col_int = periodic || (xin && yin);
-    const bool col_fx = !periodic && xg && yin;
-    const bool col_fy = !periodic && xin && yg;
-    const bool loadable_col = periodic || (x >= -1 && x <= L.nx && y >= -1 && y <= L.ny);
-    const int xw = periodic ? wrap(x, L.nx) : x;
-    const int yw = periodic ? wrap(y, L.ny) : y;
+    bool col_int = true, col_fx = false, col_fy = false, loadable = true;
+    int xw = x, yw = y;
+    if (EDGE) {
+        if (periodic) {
+            xw = wrap(x, L.nx);
+            yw = wrap(y, L.ny);
+        } else {
+            const bool xin = x >= 0 && x < L.nx, yin = y >= 0 && y < L.ny;
+            const bool xg = x == -1 || x == L.nx, yg = y == -1 || y == L.ny;
+            col_int = xin && yin;
+            col_fx = xg && yin;
+            col_fy = xin && yg;
+            loadable = x >= -1 && x <= L.nx && y >= -1 && y <= L.ny;
+        }
+    }
     const bool out_col = tx >= K && tx < TB - K && ty >= K && ty < TB - K && x >= -1 && x <= L.nx && y >= -1 &&
                          y <= L.ny;
-
-    float qh[K][3], ql[K][3], dq[K][2], rq[K + 1];
-#pragma unroll
-    for (int t = 0; t < K; ++t) {
-        qh[t][0] = qh[t][1] = qh[t][2] = 0.f;
-        ql[t][0] = ql[t][1] = ql[t][2] = 0.f;
-        dq[t][0] = dq[t][1] = 0.f;
-    }
-#pragma unroll
-    for (int t = 0; t <= K; ++t) rq[t] = 0.f;
-
-    auto load = [&](int p, float& h, float& l, float& d, float& r) {
-        h = l = d = r = 0.f;
-        if (!loadable_col) return;
-        int pw = p;
-        if (periodic) {
-            pw = wrap(p, L.nz);
-        } else if (p < -1 || p > L.nz) {
-            return;
-        }
-        const long long q = L.at(xw, yw, pw);
-        h = __ldg(P.hi_c + q);
-        l = __ldg(P.lo_c + q);
-        d = __ldg(P.d_c + q);
-        r = __ldg(P.rho + q);
-    };
-
-    float nh, nl, nd, nr;
-    load(z0 - K, nh, nl, nd, nr);
-    int lvl = 0;
-    for (int p = z0 - K; p < z1 + K; ++p) {
-        // shift level 0 in (plane p), prefetch plane p + 1
-        const float h0 = nh, l0 = nl, d0 = nd, r0 = nr;
-        if (p + 1 < z1 + K) load(p + 1, nh, nl, nd, nr);
-        qh[0][0] = qh[0][1];
-        qh[0][1] = qh[0][2];
-        qh[0][2] = h0;
-        ql[0][0] = ql[0][1];
-        ql[0][1] = ql[0][2];
-        ql[0][2] = l0;
-        dq[0][0] = dq[0][1];
-        dq[0][1] = d0;
-#pragma unroll
-        for (int t = K; t > 0; --t) rq[t] = rq[t - 1];
-        rq[0] = r0;
-
-#pragma unroll
-        for (int t = 1; t <= K; ++t) {
-            const int pt = p - t;  // plane level t computes in this iteration
-            const float c = qh[t - 1][1], lc = ql[t - 1][1];
-            const float dprev = dq[t - 1][0];
-            const int b = lvl & 1;
-            ++lvl;
-            sh[b][ty + 1][tx + 1] = make_float2(c, lc);
-            __syncthreads();
-            float oh = c, ol = lc, od = dprev;
-            const bool in_win = tx >= t && tx < TB - t && ty >= t && ty < TB - t && pt >= z0 - (K - t) &&
-                                pt < z1 + (K - t);
-            if (in_win) {
-                const bool zin = periodic || (pt >= 0 && pt < L.nz);
-                const bool zg = !periodic && (pt == -1 || pt == L.nz);
-                if (col_int && zin) {
-                    const float2 xl = sh[b][ty + 1][tx], xr = sh[b][ty + 1][tx + 2];
-                    const float2 ys = sh[b][ty][tx + 1], yn = sh[b][ty + 2][tx + 1];
-                    f32k_update(xl.x, xr.x, ys.x, yn.x, qh[t - 1][0], qh[t - 1][2], c, xl.y, xr.y, ys.y, yn.y,
-                                ql[t - 1][0], ql[t - 1][2], lc, dprev, rq[t], P.nu2, oh, ol, od);
-                } else if (robin && ((col_int && zg) || ((col_fx || col_fy) && zin))) {
-                    // Robin face ghost: inward neighbour and coefficient row
-                    float2 in;
-                    long long row;
-                    if (col_fx) {
-                        in = x < 0 ? sh[b][ty + 1][tx + 2] : sh[b][ty + 1][tx];
-                        row = P.F.off[x < 0 ? 0 : 1] + (long long)pt * L.ny + y;
-                    } else if (col_fy) {
-                        in = y < 0 ? sh[b][ty + 2][tx + 1] : sh[b][ty][tx + 1];
-                        row = P.F.off[y < 0 ? 2 : 3] + (long long)pt * L.nx + x;
-                    } else {
-                        in = pt < 0 ? make_float2(qh[t - 1][2], ql[t - 1][2]) : make_float2(qh[t - 1][0], ql[t - 1][0]);
-                        row = P.F.off[pt < 0 ? 4 : 5] + (long long)y * L.nx + x;
-                    }
-                    const float2 ab = P.robin32[row];
-                    robin_update_f32k(ab.x, ab.y, c, lc, in.x, in.y, oh, ol);
-                }
-            }
-            if (t < K) {
-                qh[t][0] = qh[t][1];
-                qh[t][1] = qh[t][2];
-                qh[t][2] = oh;
-                ql[t][0] = ql[t][1];
-                ql[t][1] = ql[t][2];
-                ql[t][2] = ol;
-                dq[t][0] = dq[t][1];
-                dq[t][1] = od;
-            } else if (out_col && pt >= z0 && pt < z1) {
-                if (periodic) {
-                    // interior cells, and the face ghosts as copies of the wrapped cells (the same values the
-                    // blocks owning those cells compute, from the same inputs)
-                    const int nout = (x < 0 || x >= L.nx) + (y < 0 || y >= L.ny) + (pt < 0 || pt >= L.nz);
-                    if (nout <= 1 && pt >= -1 && pt <= L.nz) {
-                        const long long q = L.at(x, y, pt);
-                        P.hi_n[q] = oh;
-                        P.lo_n[q] = ol;
-                        if (nout == 0) P.d_n[q] = od;
-                    }
-                } else {
-                    const bool zin = pt >= 0 && pt < L.nz;
-                    const bool zg = pt == -1 || pt == L.nz;
-                    const long long q = L.at(x, y, pt);
-                    if (col_int && zin) {
-                        P.hi_n[q] = oh;
-                        P.lo_n[q] = ol;
-                        P.d_n[q] = od;
-                    } else if (robin && ((col_int && zg) || ((col_fx || col_fy) && zin))) {
-                        P.hi_n[q] = oh;
-                        P.lo_n[q] = ol;
-                    }
-                }
-            }
-        }
-    }
-}
-
-// Fast path for blocks whose whole 32 x 32 region lies inside the domain in x and y: no per-cell classification and
-// no shrinking-window tests -- every thread updates its column at every level (cells outside the valid trapezoid
-// compute values that are never written), only the z ghost planes need a (block-uniform) branch.
-template <int K>
-__device__ __forceinline__ void fast_path(const TParams& P, float2 (*sh)[TB + 2][TB + 2]) {
-    constexpr int W = TB - 2 * K;
-    const int tx = threadIdx.x, ty = threadIdx.y;
-    const Layout& L = P.L;
-    const bool periodic = P.bc == HG_BC_PERIODIC;
-    const bool robin = P.bc == HG_BC_ROBIN;
-    const int x = -1 + (int)blockIdx.x * W + tx - K;
-    const int y = -1 + (int)blockIdx.y * W + ty - K;
-    const int z0 = -1 + (int)blockIdx.z * P.zchunk;
-    const int z1 = min(L.nz + 1, z0 + P.zchunk);
-    const bool out_col = tx >= K && tx < TB - K && ty >= K && ty < TB - K;
-    const long long col = L.at(x, y, -1) + L.plane;  // padded index of (x, y, 0)
+    const long long col = loadable ? L.at(xw, yw, 0) : 0;
     const float* hi_c = P.hi_c + col;
     const float* lo_c = P.lo_c + col;
     const float* d_c = P.d_c + col;
@@ -225,27 +100,27 @@ __device__ __forceinline__ void fast_path(const TParams& P, float2 (*sh)[TB + 2]
 #pragma unroll
     for (int t = 0; t <= K; ++t) rq[t] = 0.f;
 
-    auto load = [&](int p, float& h, float& l, float& d, float& r) {
-        int pw = p;
-        if (periodic) {
-            pw = wrap(p, L.nz);
-        } else if (p < -1 || p > L.nz) {
+    // level-0 plane p of this column; pw is p wrapped into [0, nz) for periodic boundaries
+    auto load = [&](int p, int pw, float& h, float& l, float& d, float& r) {
+        if (!loadable || (!periodic && (p < -1 || p > L.nz))) {
             h = l = d = r = 0.f;
             return;
         }
-        const long long o = (long long)pw * L.plane;
+        const long long o = (long long)(periodic ? pw : p) * L.plane;
         h = __ldg(hi_c + o);
         l = __ldg(lo_c + o);
         d = __ldg(d_c + o);
         r = __ldg(rs + o);
     };
 
+    int pw = periodic ? wrap(z0 - K, L.nz) : 0;
     float nh, nl, nd, nr;
-    load(z0 - K, nh, nl, nd, nr);
-    int lvl = 0;
+    load(z0 - K, pw, nh, nl, nd, nr);
+    int par = 0;  // parity of the shared-memory buffer for level 1 of this plane
     for (int p = z0 - K; p < z1 + K; ++p) {
         const float h0 = nh, l0 = nl, d0 = nd, r0 = nr;
-        if (p + 1 < z1 + K) load(p + 1, nh, nl, nd, nr);
+        if (periodic && ++pw == L.nz) pw = 0;
+        if (p + 1 < z1 + K) load(p + 1, pw, nh, nl, nd, nr);
         qh[0][0] = qh[0][1];
         qh[0][1] = qh[0][2];
         qh[0][2] = h0;
@@ -259,23 +134,35 @@ __device__ __forceinline__ void fast_path(const TParams& P, float2 (*sh)[TB + 2]
         rq[0] = r0;
 #pragma unroll
         for (int t = 1; t <= K; ++t) {
-            const int pt = p - t;
+            const int pt = p - t;  // plane level t computes in this iteration
             const float c = qh[t - 1][1], lc = ql[t - 1][1];
             const float dprev = dq[t - 1][0];
-            const int b = lvl & 1;
-            ++lvl;
+            const int b = par ^ ((t - 1) & 1);  // consecutive levels alternate buffers, also across planes
             sh[b][ty + 1][tx + 1] = make_float2(c, lc);
             __syncthreads();
             float oh = c, ol = lc, od = dprev;
-            if (periodic || (pt >= 0 && pt < L.nz)) {
+            const bool zin = periodic || (pt >= 0 && pt < L.nz);
+            const bool zg = !periodic && (pt == -1 || pt == L.nz);
+            if (col_int && zin) {
                 const float2 xl = sh[b][ty + 1][tx], xr = sh[b][ty + 1][tx + 2];
                 const float2 ys = sh[b][ty][tx + 1], yn = sh[b][ty + 2][tx + 1];
                 f32k_update(xl.x, xr.x, ys.x, yn.x, qh[t - 1][0], qh[t - 1][2], c, xl.y, xr.y, ys.y, yn.y,
                             ql[t - 1][0], ql[t - 1][2], lc, dprev, rq[t], P.nu2, oh, ol, od);
-            } else if (robin && (pt == -1 || pt == L.nz)) {
-                const float ih = pt < 0 ? qh[t - 1][2] : qh[t - 1][0], il = pt < 0 ? ql[t - 1][2] : ql[t - 1][0];
-                const float2 ab = P.robin32[P.F.off[pt < 0 ? 4 : 5] + (long long)y * L.nx + x];
-                robin_update_f32k(ab.x, ab.y, c, lc, ih, il, oh, ol);
+            } else if (robin && ((col_int && zg) || (EDGE && (col_fx || col_fy) && zin))) {
+                float2 in;
+                long long row;
+                if (EDGE && col_fx) {
+                    in = x < 0 ? sh[b][ty + 1][tx + 2] : sh[b][ty + 1][tx];
+                    row = P.F.off[x < 0 ? 0 : 1] + (long long)pt * L.ny + y;
+                } else if (EDGE && col_fy) {
+                    in = y < 0 ? sh[b][ty + 2][tx + 1] : sh[b][ty][tx + 1];
+                    row = P.F.off[y < 0 ? 2 : 3] + (long long)pt * L.nx + x;
+                } else {
+                    in = pt < 0 ? make_float2(qh[t - 1][2], ql[t - 1][2]) : make_float2(qh[t - 1][0], ql[t - 1][0]);
+                    row = P.F.off[pt < 0 ? 4 : 5] + (long long)y * L.nx + x;
+                }
+                const float2 ab = P.robin32[row];
+                robin_update_f32k(ab.x, ab.y, c, lc, in.x, in.y, oh, ol);
             }
             if (t < K) {
                 qh[t][0] = qh[t][1];
@@ -287,31 +174,40 @@ __device__ __forceinline__ void fast_path(const TParams& P, float2 (*sh)[TB + 2]
                 dq[t][0] = dq[t][1];
                 dq[t][1] = od;
             } else if (out_col && pt >= z0 && pt < z1) {
-                const long long q = col + (long long)pt * L.plane;
-                const bool zin = pt >= 0 && pt < L.nz;
-                if (zin) {
+                const long long q = L.at(x, y, pt);
+                if (periodic) {
+                    // interior cells, and the face ghosts as copies of the wrapped cells (the same values the
+                    // blocks owning those cells compute, from the same inputs)
+                    const int nout = (x < 0 || x >= L.nx) + (y < 0 || y >= L.ny) + (pt < 0 || pt >= L.nz);
+                    if (nout <= 1 && pt >= -1 && pt <= L.nz) {
+                        P.hi_n[q] = oh;
+                        P.lo_n[q] = ol;
+                        if (nout == 0) P.d_n[q] = od;
+                    }
+                } else if (col_int && zin) {
                     P.hi_n[q] = oh;
                     P.lo_n[q] = ol;
                     P.d_n[q] = od;
-                } else if ((robin || periodic) && (pt == -1 || pt == L.nz)) {
-                    P.hi_n[q] = oh;  // Robin ghost update, or (periodic) the copy of the wrapped plane
+                } else if (robin && ((col_int && zg) || (EDGE && (col_fx || col_fy) && zin))) {
+                    P.hi_n[q] = oh;
                     P.lo_n[q] = ol;
                 }
             }
         }
+        if (K & 1) par ^= 1;
     }
 }
 
 template <int K>
 __global__ void __launch_bounds__(TB* TB, 1) k_temporal_f32k(const TParams P) {
     constexpr int W = TB - 2 * K;
-    __shared__ float2 sh[2][TB + 2][TB + 2];  // padded: edge threads of the fast path read (unused) padding
+    __shared__ float2 sh[2][TB + 2][TB + 2];  // padded by one cell: edge threads read (unused) padding
     const int xr0 = -1 + (int)blockIdx.x * W - K, yr0 = -1 + (int)blockIdx.y * W - K;
     const bool inside = xr0 >= 0 && xr0 + TB <= P.L.nx && yr0 >= 0 && yr0 + TB <= P.L.ny;
     if (inside)
-        fast_path<K>(P, sh);
+        region_sweep<K, false>(P, sh);
     else
-        general_path<K>(P, sh);
+        region_sweep<K, true>(P, sh);
 }
 
 template <int K>

@@ -1,20 +1,47 @@
-"""Summarise an ncu launch list (--metrics gpu__time_duration.sum --csv) into per-kernel launches, time and share.
+"""Summaries of Nsight Compute output for the notes under profiles/.
 
-usage: python -m paper_1602_05700_gb300.ncu_summary launches.csv
+  python -m paper_1602_05700_gb300.ncu_summary launches.csv
+      per-kernel launches, total time and share of an ncu launch list (--metrics gpu__time_duration.sum --csv)
+  python -m paper_1602_05700_gb300.ncu_summary --report capture.ncu-rep
+      the headline counters of each captured launch (reads the report with `ncu -i ... --page raw --csv`)
 """
 import collections
 import csv
+import io
+import subprocess
 import sys
 
 SCALE = {"ns": 1e-6, "nsecond": 1e-6, "us": 1e-3, "usecond": 1e-3, "ms": 1.0, "msecond": 1.0, "s": 1e3, "second": 1e3}
 
+REPORT_METRICS = [
+    ("gpu__time_duration.sum", "duration"),
+    ("dram__bytes_read.sum", "DRAM read"),
+    ("dram__bytes_write.sum", "DRAM write"),
+    ("gpu__dram_throughput.avg.pct_of_peak_sustained_elapsed", "DRAM throughput % of peak"),
+    ("lts__t_sector_hit_rate.pct", "L2 hit rate %"),
+    ("sm__throughput.avg.pct_of_peak_sustained_elapsed", "SM throughput %"),
+    ("smsp__issue_active.avg.pct_of_peak_sustained_active", "issue active %"),
+    ("sm__pipe_fma_cycles_active.avg.pct_of_peak_sustained_active", "FMA pipe %"),
+    ("sm__pipe_alu_cycles_active.avg.pct_of_peak_sustained_active", "ALU pipe %"),
+    ("sm__pipe_fp64_cycles_active.avg.pct_of_peak_sustained_active", "FP64 pipe %"),
+    ("sm__pipe_tensor_cycles_active.avg.pct_of_peak_sustained_active", "tensor pipe %"),
+    ("sm__warps_active.avg.pct_of_peak_sustained_active", "warps active %"),
+    ("launch__registers_per_thread", "registers/thread"),
+    ("launch__occupancy_limit_registers", "blocks/SM (register limit)"),
+    ("launch__grid_size", "grid"),
+    ("launch__block_size", "block"),
+    ("smsp__average_warps_issue_stalled_long_scoreboard_per_issue_active.ratio", "stall long scoreboard"),
+    ("smsp__average_warps_issue_stalled_barrier_per_issue_active.ratio", "stall barrier"),
+    ("smsp__average_warps_issue_stalled_math_pipe_throttle_per_issue_active.ratio", "stall math pipe"),
+    ("smsp__inst_executed.sum", "warp instructions"),
+]
+
 
 def short(name: str) -> str:
-    base = name.split("(")[0]
-    return base.replace("void ", "").strip()
+    return name.split("(")[0].replace("void ", "").strip()
 
 
-def main(path):
+def launches(path):
     rows = list(csv.reader(open(path)))
     h = next(i for i, r in enumerate(rows) if "Kernel Name" in r)
     hdr = rows[h]
@@ -26,11 +53,28 @@ def main(path):
         agg[short(r[ki])][0] += 1
         agg[short(r[ki])][1] += float(r[vi].replace(",", "")) * SCALE[r[ui]]
     tot = sum(a[1] for a in agg.values())
-    print(f"{'kernel':70s} {'launches':>8s} {'total ms':>10s} {'share':>7s}")
+    print(f"| kernel | launches | total ms | share |\n|---|---|---|---|")
     for k, (n, t) in sorted(agg.items(), key=lambda x: -x[1][1]):
-        print(f"{k[:70]:70s} {n:8d} {t:10.3f} {100 * t / tot:6.2f}%")
-    print(f"{'total':70s} {sum(a[0] for a in agg.values()):8d} {tot:10.3f}")
+        print(f"| `{k}` | {n} | {t:.3f} | {100 * t / tot:.2f}% |")
+    print(f"| total | {sum(a[0] for a in agg.values())} | {tot:.3f} | |")
+
+
+def report(path):
+    out = subprocess.run(["ncu", "-i", path, "--page", "raw", "--csv"], capture_output=True, text=True, check=True)
+    rows = list(csv.reader(io.StringIO(out.stdout)))
+    hdr, units = rows[0], rows[1]
+    for launch in rows[2:]:
+        name = short(launch[hdr.index("Kernel Name")]) if "Kernel Name" in hdr else "?"
+        print(f"launch: `{name}`\n\n| counter | value |\n|---|---|")
+        for metric, label in REPORT_METRICS:
+            if metric in hdr:
+                i = hdr.index(metric)
+                print(f"| {label} (`{metric}`) | {launch[i]} {units[i]} |")
+        print()
 
 
 if __name__ == "__main__":
-    main(sys.argv[1])
+    if len(sys.argv) == 3 and sys.argv[1] == "--report":
+        report(sys.argv[2])
+    else:
+        launches(sys.argv[1])
