@@ -9,8 +9,9 @@ boundary.  Per step: hg_set_density (rho of that hydro time, resident in HBM), 2
 Metric: Gcell-updates/s = 512^3 x 20 x steps / time (whole job, all ranks), FP32 with compensated increments;
 the FP64 reference mode is measured on the same workload and reported beside it.  `roofline` is the sub-step
 kernel's algorithmic bytes per launch / its CUDA-event duration inside the timed region, against the measured
-copy bandwidth.  `e2e` repeats the measurement through the public API with the density coming from pinned host
-memory and the acceleration copied back every step.  `--impl reference` times the CPU oracle instead.
+copy bandwidth.  `e2e` repeats the measurement through the public API (hg_io_step) with each step's density
+coming from pinned host memory and the acceleration copied back to pinned host memory every step.
+`--impl reference` times the CPU oracle instead.
 
 Multi-GPU: the path has no exchange step in this build (one independent grid per rank), so N ranks run N
 independent problems (weak scaling, no collective on the data path).
@@ -259,37 +260,34 @@ def run_ours(args, rank, world, local_rank):
                                      "hbm_frac": round(hbm64 / hbm_peak, 4), "kernel": "k_step_f64",
                                      "avg_launch_ms": round(avg64, 5)},
                         "gpu_launches": r64["launches"]}
-    # end to end through the public API: density from pinned host memory, acceleration back to the host
+    # end to end through the public API: each step's density from pinned host memory, -grad phi back to pinned
+    # host memory, with the copies of one step overlapping the sub-steps of the next (hg_io_step / hg_io_wait)
     if not args.skip_e2e:
-        ke = max(2, min(steps, 5))
-        host_rho = [rhos[s].cpu().pin_memory() for s in range(min(2, len(rhos)))]
-        host_acc = [torch.empty((n, n, n), dtype=torch.float32).pin_memory() for _ in range(3)]
+        ke, we = max(4, min(steps, 10)), 2
+        host_rho = [rhos[s % len(rhos)].cpu().pin_memory() for s in range(we + ke)]
+        host_acc = [[torch.empty((n, n, n), dtype=torch.float32).pin_memory() for _ in range(3)] for _ in range(2)]
         g = hg.Grid(n, n, n, W["h"], W["origin"], W["c"], W["G"], W["dt"], "f32k", "robin")
         if best > 1:
             g.set_temporal_depth(best)
-        out = [torch.empty((n, n, n), device=dev, dtype=torch.float32) for _ in range(3)]
 
-        def e2e_step(s):
-            g.set_density(host_rho[s % len(host_rho)])
-            g.step(N_SUB)
-            g.accel(out=out)
-            for a, b in zip(host_acc, out):
-                a.copy_(b, non_blocking=True)
-            torch.cuda.current_stream().synchronize()
+        def e2e_steps(first, count):
+            for s in range(first, first + count):
+                g.io_step(host_rho[s], N_SUB, host_acc[s % 2])
+                g.io_wait(1)  # step s-1 is done: its outputs are on the host, its buffers free again
+            g.io_wait(0)
 
-        for s in range(2):
-            e2e_step(s)
+        e2e_steps(0, we)
         barrier()
         t0 = time.perf_counter()
-        for s in range(ke):
-            e2e_step(s)
+        e2e_steps(we, ke)
         barrier()
         sec = max_over_ranks(time.perf_counter() - t0)
         g.free()
         line["e2e"] = {"value": round(cells * N_SUB * ke * world / sec / 1e9, 3), "unit": "Gcell-updates/s",
                        "h2d_bytes_per_step": 4 * cells, "d2h_bytes_per_step": 12 * cells, "steps": ke,
                        "temporal_depth": best,
-                       "note": "pinned host density in, pinned host -grad phi out, every step"}
+                       "note": "each step: its density from pinned host memory in, -grad phi (3 x f32) out to "
+                               "pinned host memory; copies overlap the neighbouring steps' sub-steps"}
     if rank == 0 and not args.skip_cpu:
         line["cpu_baseline"] = cpu_baseline(args.n, args.cpu_substeps)
     multi.finalize()

@@ -93,7 +93,10 @@ int hg_init_grid(hg_grid** g, int nx, int ny, int nz, double h, const double ori
  * Set the density (Sec. 2: rho is frozen during the wave sub-steps of one hydro step).  rho: nz*ny*nx values of
  * type dtype, host or device.  Recomputes the FP64 mass, the mean (periodic) and, for the Dirichlet modes, the
  * FP64 multipole moments and the ghost values of phi^n and phi^{n-1} (Sec. 4, Dirichlet boundary by multipole
- * expansion).  The interior of phi is not touched.
+ * expansion).  The interior of phi is not touched.  With a device density the call does not wait for the GPU
+ * (except in the Dirichlet modes, whose moments come back to the host): the mass and mean are read back lazily
+ * by the next call that reports them (hg_get_stats, hg_save_state), and rho must stay valid until the grid's
+ * stream has run the work.  With a host density the call returns after the copy has been consumed.
  */
 int hg_set_density(hg_grid* g, const void* rho, int dtype, int on_device);
 
@@ -185,7 +188,29 @@ int hg_adjoint_grad(hg_grid* g, void* dL_drho, int dtype, int on_device);
 int hg_profile(hg_grid* g, int enable);
 int hg_profile_read(hg_grid* g, double* substep_kernel_ms, long long* substep_launches, long long* kernel_launches);
 
-/* Block until the grid's stream is idle; HG_ERR_CUDA carries any pending asynchronous error. */
+/*
+ * One hydro step's gravity with host input and output, pipelined across calls (Sec. 2: rho frozen over the
+ * sub-steps of a hydro step, -grad phi handed back to the hydro code).  Enqueues, without waiting for the GPU:
+ *   the copy of rho_host (nz*ny*nx values of rho_dtype) to a device slot on an upload stream of the grid,
+ *   hg_set_density from that slot, n_substeps sub-steps (hg_step), -grad phi (hg_accel, central differences) into
+ *   a device slot, and its copy to ax_host, ay_host, az_host (nz*ny*nx values of acc_dtype each) on a download
+ *   stream of the grid.
+ * Two slots alternate, so the upload of call s+1 and the download of call s overlap the sub-steps of the other
+ * call; the grid's stream waits only on the upload it consumes, and a slot is refilled only after its previous
+ * contents have been used.  rho_host may be NULL (the source is unchanged) and the three acceleration pointers
+ * may all be NULL (no output).  The host buffers must be page-locked for the copies to overlap (pageable memory
+ * works, synchronously) and belong to the library until hg_io_wait has covered the call.  Device memory: two
+ * density slots and two acceleration slots, allocated on first use.  Errors: HG_ERR_ARG (bad dtype, only some
+ * acceleration pointers), HG_ERR_CUDA.
+ */
+int hg_io_step(hg_grid* g, const void* rho_host, int rho_dtype, int n_substeps, void* ax_host, void* ay_host,
+               void* az_host, int acc_dtype);
+
+/* Block until all but the newest `keep` hg_io_step calls have finished (their host buffers are then the caller's
+ * again and the accelerations are in place).  keep = 0 waits for every call. */
+int hg_io_wait(hg_grid* g, int keep);
+
+/* Block until the grid's streams are idle; HG_ERR_CUDA carries any pending asynchronous error. */
 int hg_sync(hg_grid* g);
 
 /* Release the grid and its device memory (NULL is allowed). */

@@ -59,6 +59,15 @@ def _buffer(x, want_dtype=None):
     return ctypes.c_void_p(a.ctypes.data), code, 0, a
 
 
+def _writable_host(x) -> bool:
+    """True for a contiguous float32/float64 host tensor or array (one the library can write in place)."""
+    torch = _torch()
+    if isinstance(x, torch.Tensor):
+        return not x.is_cuda and x.is_contiguous() and x.dtype in (torch.float32, torch.float64)
+    return isinstance(x, np.ndarray) and x.flags.c_contiguous and x.flags.writeable and \
+        x.dtype in (np.float32, np.float64)
+
+
 class Grid:
     """One grid of nx*ny*nz cells of side h (lower corner `origin`), wave speed c, constant G, sub-step dt."""
 
@@ -80,6 +89,7 @@ class Grid:
         self.c, self.G, self.dt = float(c), float(G), float(dt)
         self.precision, self.bc, self.lmax = prec, bcc, int(lmax)
         self.device = torch.device("cuda", torch.cuda.current_device())
+        self._io_keep = []  # buffers of io_step calls not yet covered by io_wait
 
     @classmethod
     def unit_cube(cls, n, c=1.0, G=1.0, cfl=0.5, precision="f32k", bc="robin", lmax=0, ny=None, nz=None, stream=None):
@@ -139,6 +149,41 @@ class Grid:
         code = HG_DT_F64 if dtype == torch.float64 else HG_DT_F32
         _lib.check(_lib.lib().hg_accel(self.handle, *[ctypes.c_void_p(t.data_ptr()) for t in out], code))
         return tuple(out)
+
+    def io_step(self, rho=None, n=1, out=None):
+        """One hydro step with host buffers, pipelined: upload rho (host, nz*ny*nx), n sub-steps, -grad phi into
+        `out` (three host arrays or tensors of the grid shape, one dtype).  Returns before the GPU is done; the
+        buffers are in use until io_wait covers this call (io_wait(1) after each call keeps one step in flight)."""
+        keep = []
+        rp, rcode = ctypes.c_void_p(0), HG_DT_F32
+        if rho is not None:
+            rp, rcode, dev, k = _buffer(rho)
+            self._check_size(k)
+            if dev:
+                raise HGError(-1, "io_step takes host buffers (use set_density for device data)")
+            keep.append(k)
+        ptrs, acode = [ctypes.c_void_p(0)] * 3, HG_DT_F32
+        if out is not None:
+            ptrs, codes = [], set()
+            for o in out:
+                if not _writable_host(o):
+                    raise HGError(-1, "io_step outputs must be contiguous float32/float64 host buffers")
+                p, code, _, k = _buffer(o)
+                self._check_size(k)
+                ptrs.append(p)
+                codes.add(code)
+                keep.append(k)
+            if len(ptrs) != 3 or len(codes) != 1:
+                raise HGError(-1, "io_step takes three outputs of one dtype")
+            acode = codes.pop()
+        _lib.check(_lib.lib().hg_io_step(self.handle, rp, rcode, int(n), *ptrs, acode))
+        self._io_keep.append(keep)
+
+    def io_wait(self, keep=0):
+        """Block until all but the newest `keep` io_step calls are done (their outputs are then filled)."""
+        _lib.check(_lib.lib().hg_io_wait(self.handle, int(keep)))
+        while len(self._io_keep) > keep:
+            self._io_keep.pop(0)
 
     def phi(self, dtype=None, device="cuda"):
         """phi^n on the interior as an (nz, ny, nx) tensor (device) or numpy array (device='cpu')."""

@@ -52,9 +52,11 @@ __device__ __forceinline__ void two_sum_acc(float& s, float& c, float x) {
 
 template <typename TS, typename TD, bool SUM>
 __global__ void __launch_bounds__(kThreads) k_pack(const TS* __restrict__ src, TD* __restrict__ dst, Layout L,
-                                                   double shift, double scale, double* partial) {
+                                                   const double* __restrict__ sum, double count, double scale,
+                                                   double* partial) {
     float fs = 0.f, fc = 0.f;  // compensated float accumulator (float input)
     double ds = 0.0;           // double accumulator (double input)
+    const double shift = sum ? *sum / count : 0.0;  // rho_bar = sum(rho) / cells, read on the device (no host sync)
     const float scale32 = (float)scale, shift32 = (float)shift;
     if constexpr (sizeof(TS) == 4 && sizeof(TD) == 4) {
         if ((L.nx & 3) == 0 && ((uintptr_t)src & 15) == 0) {  // 16-byte groups on both sides
@@ -369,38 +371,50 @@ inline unsigned cells_blocks(const hg_grid* g) {
 }  // namespace
 
 template <bool SUM>
-static int launch_pack(hg_grid* g, const void* src, int dtype, double shift, double scale) {
+static int launch_pack(hg_grid* g, const void* src, int dtype, const double* sum, double scale) {
     const unsigned blocks = SUM ? (unsigned)kPackBlocks : cells_blocks(g);
+    const double count = (double)g->nx * g->ny * g->nz;
     if (dtype == HG_DT_F32 && g->prec == HG_PREC_F32K)
-        k_pack<float, float, SUM><<<blocks, kThreads, 0, g->stream>>>((const float*)src, (float*)g->rho, g->L, shift,
-                                                                      scale, g->red);
+        k_pack<float, float, SUM><<<blocks, kThreads, 0, g->stream>>>((const float*)src, (float*)g->rho, g->L, sum,
+                                                                      count, scale, g->red);
     else if (dtype == HG_DT_F32)
-        k_pack<float, double, SUM><<<blocks, kThreads, 0, g->stream>>>((const float*)src, (double*)g->rho, g->L, shift,
-                                                                       scale, g->red);
+        k_pack<float, double, SUM><<<blocks, kThreads, 0, g->stream>>>((const float*)src, (double*)g->rho, g->L, sum,
+                                                                       count, scale, g->red);
     else if (g->prec == HG_PREC_F32K)
-        k_pack<double, float, SUM><<<blocks, kThreads, 0, g->stream>>>((const double*)src, (float*)g->rho, g->L, shift,
-                                                                       scale, g->red);
+        k_pack<double, float, SUM><<<blocks, kThreads, 0, g->stream>>>((const double*)src, (float*)g->rho, g->L, sum,
+                                                                       count, scale, g->red);
     else
         k_pack<double, double, SUM><<<blocks, kThreads, 0, g->stream>>>((const double*)src, (double*)g->rho, g->L,
-                                                                        shift, scale, g->red);
+                                                                        sum, count, scale, g->red);
     HG_LAUNCHED("source preparation kernel");
     return HG_OK;
 }
 
-// Store the scaled source s = (c dt)^2 4 pi G (rho - rho_bar) and return sum(rho) (FP64-accurate).  Periodic
-// boundaries need the mean before scaling: a sum pass, then the pack; otherwise one fused pass.
-int prepare_source(hg_grid* g, const void* src, int dtype, double* sum_host) {
+// Store the scaled source s = (c dt)^2 4 pi G (rho - rho_bar) and leave sum(rho) (FP64-accurate) in g->dsum on the
+// device; nothing here waits for the GPU.  Periodic boundaries need the mean before scaling: a sum pass, then the
+// pack reading the sum from device memory; otherwise one fused pass.
+int prepare_source(hg_grid* g, const void* src, int dtype) {
     int rc;
+    g->mass_pending = 1;
     if (g->bc == HG_BC_PERIODIC) {
-        if ((rc = reduce_sum(g, src, dtype, sum_host))) return rc;
-        const double mean = *sum_host / ((double)g->nx * g->ny * g->nz);
-        return launch_pack<false>(g, src, dtype, mean, g->src);
+        if ((rc = reduce_sum(g, src, dtype, g->dsum))) return rc;
+        return launch_pack<false>(g, src, dtype, g->dsum, g->src);
     }
-    if ((rc = launch_pack<true>(g, src, dtype, 0.0, g->src))) return rc;
-    k_finish_mixed<<<1, kThreads, 0, g->stream>>>(g->red, kPackBlocks, 1, 0u, g->dres);
+    if ((rc = launch_pack<true>(g, src, dtype, nullptr, g->src))) return rc;
+    k_finish_mixed<<<1, kThreads, 0, g->stream>>>(g->red, kPackBlocks, 1, 0u, g->dsum);
     HG_LAUNCHED("sum finish kernel");
-    HG_CUDA(cudaMemcpyAsync(sum_host, g->dres, sizeof(double), cudaMemcpyDeviceToHost, g->stream));
+    return HG_OK;
+}
+
+// Bring the mass and mean density of the last hg_set_density to the host (waits for the stream once per density)
+int sync_mass(hg_grid* g) {
+    if (!g->mass_pending) return HG_OK;
+    double sum = 0.0;
+    HG_CUDA(cudaMemcpyAsync(&sum, g->dsum, sizeof(double), cudaMemcpyDeviceToHost, g->stream));
     HG_CUDA(cudaStreamSynchronize(g->stream));
+    g->mass = sum * g->h * g->h * g->h;
+    g->rho_bar = g->bc == HG_BC_PERIODIC ? sum / ((double)g->nx * g->ny * g->nz) : 0.0;
+    g->mass_pending = 0;
     return HG_OK;
 }
 
@@ -441,6 +455,8 @@ int accel(hg_grid* g, void* ax, void* ay, void* az, int dtype) {
 }
 
 int stats(hg_grid* g, hg_stats* s) {
+    int rc = sync_mass(g);
+    if (rc) return rc;
     k_stats<<<kRedBlocks, kThreads, 0, g->stream>>>(g->prec, g->phi[g->cur], g->lo[g->cur], g->phi[1 - g->cur],
                                                     g->dlt[g->dcur], g->rho, g->L, 1.0 / (g->h * g->h),
                                                     1.0 / ((g->c * g->dt) * (g->c * g->dt)), g->red);
@@ -476,14 +492,12 @@ int compare(hg_grid* g, const double* P, double out[3]) {
     return HG_OK;
 }
 
-int reduce_sum(hg_grid* g, const void* dense, int dtype, double* out_host) {
+int reduce_sum(hg_grid* g, const void* dense, int dtype, double* out_dev) {
     long long n = (long long)g->nx * g->ny * g->nz;
     k_sum<<<kPackBlocks, kThreads, 0, g->stream>>>(dense, dtype, n, g->red);
     HG_LAUNCHED("sum kernel");
-    k_finish_mixed<<<1, kThreads, 0, g->stream>>>(g->red, kPackBlocks, 1, 0u, g->dres);
+    k_finish_mixed<<<1, kThreads, 0, g->stream>>>(g->red, kPackBlocks, 1, 0u, out_dev);
     HG_LAUNCHED("sum finish kernel");
-    HG_CUDA(cudaMemcpyAsync(out_host, g->dres, sizeof(double), cudaMemcpyDeviceToHost, g->stream));
-    HG_CUDA(cudaStreamSynchronize(g->stream));
     return HG_OK;
 }
 

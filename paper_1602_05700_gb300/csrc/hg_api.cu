@@ -99,9 +99,15 @@ extern "C" void hg_free(hg_grid* g);
 static void release(hg_grid* g) {
     if (g->adj) hg_free(g->adj);
     void* ptrs[] = {g->phi[0], g->phi[1], g->lo[0], g->lo[1], g->dlt[0], g->dlt[1], g->rho, g->robin, g->robin32,
-                    g->red, g->dres, g->staging, g->acc[0], g->acc[1]};
+                    g->red, g->dres, g->staging, g->acc[0], g->acc[1], g->io_rho[0], g->io_rho[1], g->io_acc[0],
+                    g->io_acc[1]};
     for (void* p : ptrs)
         if (p) cudaFree(p);
+    for (auto& slot : g->io_ev)
+        for (cudaEvent_t ev : slot)
+            if (ev) cudaEventDestroy(ev);
+    if (g->io_up) cudaStreamDestroy(g->io_up);
+    if (g->io_down) cudaStreamDestroy(g->io_down);
     if (g->prof_ev) {
         for (int e = 0; e < 2 * kProfPairs; ++e) cudaEventDestroy(g->prof_ev[e]);
         delete[] g->prof_ev;
@@ -234,8 +240,10 @@ int hg_init_grid(hg_grid** out, int nx, int ny, int nz, double h, const double o
     if (rc == HG_OK) {
         g->red_elems = reduction_scratch_elems();
         e = cudaMalloc(&g->red, (size_t)g->red_elems * sizeof(double));
-        if (e == cudaSuccess) e = cudaMalloc(&g->dres, kMaxQ * sizeof(double));
+        if (e == cudaSuccess) e = cudaMalloc(&g->dres, (kMaxQ + 1) * sizeof(double));
+        if (e == cudaSuccess) e = cudaMemsetAsync(g->dres, 0, (kMaxQ + 1) * sizeof(double), g->stream);
         if (e != cudaSuccess) rc = cuda_fail(e, "cudaMalloc(reduction scratch)");
+        g->dsum = g->dres + kMaxQ;
     }
     if (rc == HG_OK) {
         e = cudaStreamSynchronize(g->stream);
@@ -247,6 +255,18 @@ int hg_init_grid(hg_grid** out, int nx, int ny, int nz, double h, const double o
         return rc;
     }
     *out = g;
+    return HG_OK;
+}
+
+// density already on the device -> stored source, sum(rho) on the device, and for the Dirichlet modes the moments
+// and boundary data; asynchronous except for the Dirichlet moments (read back to the host)
+static int set_density_device(hg_grid* g, const void* src, int dtype) {
+    int rc;
+    if ((rc = prepare_source(g, src, dtype))) return rc;
+    if (g->bc == HG_BC_DIRICHLET_ANALYTIC || g->bc == HG_BC_DIRICHLET_MULTIPOLE) {
+        if ((rc = compute_moments(g, src, dtype))) return rc;
+        if ((rc = set_ghosts_dirichlet(g))) return rc;
+    }
     return HG_OK;
 }
 
@@ -262,14 +282,7 @@ int hg_set_density(hg_grid* g, const void* rho, int dtype, int on_device) {
         HG_CUDA(cudaMemcpyAsync(g->staging, rho, (size_t)n * dt_size(dtype), cudaMemcpyHostToDevice, g->stream));
         src = g->staging;
     }
-    double sum = 0.0;
-    if ((rc = prepare_source(g, src, dtype, &sum))) return rc;
-    g->mass = sum * g->h * g->h * g->h;
-    g->rho_bar = g->bc == HG_BC_PERIODIC ? sum / (double)n : 0.0;
-    if (g->bc == HG_BC_DIRICHLET_ANALYTIC || g->bc == HG_BC_DIRICHLET_MULTIPOLE) {
-        if ((rc = compute_moments(g, src, dtype))) return rc;
-        if ((rc = set_ghosts_dirichlet(g))) return rc;
-    }
+    if ((rc = set_density_device(g, src, dtype))) return rc;
     if (!on_device) HG_CUDA(cudaStreamSynchronize(g->stream));  // the staging buffer is reused by later calls
     return HG_OK;
 }
@@ -450,6 +463,7 @@ int hg_save_state(hg_grid* g, void* buf, int on_device) {
     H.cur = g->cur;
     H.have_Q = g->have_Q;
     H.step = g->step;
+    if ((rc = sync_mass(g))) return rc;
     H.mass = g->mass;
     H.rho_bar = g->rho_bar;
     memcpy(H.Q, g->Q, sizeof H.Q);
@@ -488,6 +502,7 @@ int hg_load_state(hg_grid* g, const void* buf, int on_device) {
     g->step = H.step;
     g->mass = H.mass;
     g->rho_bar = H.rho_bar;
+    g->mass_pending = 0;
     memcpy(g->Q, H.Q, sizeof H.Q);
     return HG_OK;
 }
@@ -594,10 +609,108 @@ int hg_adjoint_grad(hg_grid* g, void* dL_drho, int dtype, int on_device) {
     return HG_OK;
 }
 
+// ---- host I/O pipeline ----
+static size_t align_up(size_t b, size_t a) { return (b + a - 1) / a * a; }
+
+static int io_ready(hg_grid* g, size_t rho_bytes, size_t acc_bytes) {
+    if (!g->io_up) {
+        HG_CUDA(cudaStreamCreateWithFlags(&g->io_up, cudaStreamNonBlocking));
+        HG_CUDA(cudaStreamCreateWithFlags(&g->io_down, cudaStreamNonBlocking));
+        for (auto& slot : g->io_ev)
+            for (cudaEvent_t& ev : slot) HG_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    }
+    if (rho_bytes <= g->io_rho_bytes && acc_bytes <= g->io_acc_bytes) return HG_OK;
+    // the slots grow (a wider dtype) only while nothing of the pipeline is in flight
+    HG_CUDA(cudaStreamSynchronize(g->stream));
+    HG_CUDA(cudaStreamSynchronize(g->io_up));
+    HG_CUDA(cudaStreamSynchronize(g->io_down));
+    if (rho_bytes > g->io_rho_bytes) {
+        for (void*& p : g->io_rho) {
+            if (p) HG_CUDA(cudaFree(p));
+            p = nullptr;
+        }
+        g->io_rho_bytes = 0;
+        for (void*& p : g->io_rho) HG_CUDA(cudaMalloc(&p, rho_bytes));
+        g->io_rho_bytes = rho_bytes;
+    }
+    if (acc_bytes > g->io_acc_bytes) {
+        for (void*& p : g->io_acc) {
+            if (p) HG_CUDA(cudaFree(p));
+            p = nullptr;
+        }
+        g->io_acc_bytes = 0;
+        for (void*& p : g->io_acc) HG_CUDA(cudaMalloc(&p, acc_bytes));
+        g->io_acc_bytes = acc_bytes;
+    }
+    return HG_OK;
+}
+
+int hg_io_step(hg_grid* g, const void* rho_host, int rho_dtype, int n_substeps, void* ax_host, void* ay_host,
+               void* az_host, int acc_dtype) {
+    int rc = check_grid(g);
+    if (rc) return rc;
+    if (n_substeps < 0) return fail(HG_ERR_ARG, "n_substeps must be >= 0");
+    const bool want_acc = ax_host || ay_host || az_host;
+    if (want_acc && !(ax_host && ay_host && az_host)) return fail(HG_ERR_ARG, "give all three acceleration buffers");
+    if (rho_host && rho_dtype != HG_DT_F32 && rho_dtype != HG_DT_F64)
+        return fail(HG_ERR_ARG, "unknown density dtype %d", rho_dtype);
+    if (want_acc && acc_dtype != HG_DT_F32 && acc_dtype != HG_DT_F64)
+        return fail(HG_ERR_ARG, "unknown acceleration dtype %d", acc_dtype);
+    const size_t n = (size_t)g->nx * g->ny * g->nz;
+    const size_t rho_bytes = rho_host ? n * dt_size(rho_dtype) : 0;
+    const size_t comp = want_acc ? align_up(n * dt_size(acc_dtype), 256) : 0;  // one component, 256-byte aligned
+    if ((rc = io_ready(g, rho_bytes, 3 * comp))) return rc;
+    const int k = (int)(g->io_issued & 1);
+    cudaEvent_t* ev = g->io_ev[k];  // 0 uploaded, 1 consumed, 2 acceleration written, 3 step complete
+    if (rho_host) {
+        HG_CUDA(cudaStreamWaitEvent(g->io_up, ev[1], 0));  // the slot's previous density has been packed
+        HG_CUDA(cudaMemcpyAsync(g->io_rho[k], rho_host, rho_bytes, cudaMemcpyHostToDevice, g->io_up));
+        HG_CUDA(cudaEventRecord(ev[0], g->io_up));
+        HG_CUDA(cudaStreamWaitEvent(g->stream, ev[0], 0));
+        if ((rc = set_density_device(g, g->io_rho[k], rho_dtype))) return rc;
+        HG_CUDA(cudaEventRecord(ev[1], g->stream));
+    }
+    if ((rc = hg_step(g, n_substeps))) return rc;
+    char* a = (char*)g->io_acc[k];
+    if (want_acc) {
+        HG_CUDA(cudaStreamWaitEvent(g->stream, ev[3], 0));  // the slot's previous acceleration has been downloaded
+        if ((rc = accel(g, a, a + comp, a + 2 * comp, acc_dtype))) return rc;
+    }
+    HG_CUDA(cudaEventRecord(ev[2], g->stream));
+    HG_CUDA(cudaStreamWaitEvent(g->io_down, ev[2], 0));
+    if (want_acc) {
+        const size_t bytes = n * dt_size(acc_dtype);
+        HG_CUDA(cudaMemcpyAsync(ax_host, a, bytes, cudaMemcpyDeviceToHost, g->io_down));
+        HG_CUDA(cudaMemcpyAsync(ay_host, a + comp, bytes, cudaMemcpyDeviceToHost, g->io_down));
+        HG_CUDA(cudaMemcpyAsync(az_host, a + 2 * comp, bytes, cudaMemcpyDeviceToHost, g->io_down));
+    }
+    HG_CUDA(cudaEventRecord(ev[3], g->io_down));
+    ++g->io_issued;
+    return HG_OK;
+}
+
+int hg_io_wait(hg_grid* g, int keep) {
+    int rc = check_grid(g);
+    if (rc) return rc;
+    if (keep < 0) return fail(HG_ERR_ARG, "keep must be >= 0");
+    // a slot's completion event is re-recorded two calls later, so waiting on it is exact for the last two calls
+    // and conservative (waits longer) for older ones
+    while (g->io_waited < g->io_issued - keep) {
+        HG_CUDA(cudaEventSynchronize(g->io_ev[g->io_waited & 1][3]));
+        ++g->io_waited;
+    }
+    return HG_OK;
+}
+
 int hg_sync(hg_grid* g) {
     int rc = check_grid(g);
     if (rc) return rc;
     HG_CUDA(cudaStreamSynchronize(g->stream));
+    if (g->io_up) {
+        HG_CUDA(cudaStreamSynchronize(g->io_up));
+        HG_CUDA(cudaStreamSynchronize(g->io_down));
+        g->io_waited = g->io_issued;
+    }
     HG_CUDA(cudaGetLastError());
     return HG_OK;
 }
@@ -606,6 +719,8 @@ void hg_free(hg_grid* g) {
     if (!g) return;
     cudaSetDevice(g->device);
     cudaStreamSynchronize(g->stream);
+    if (g->io_up) cudaStreamSynchronize(g->io_up);
+    if (g->io_down) cudaStreamSynchronize(g->io_down);
     release(g);
     delete g;
 }

@@ -121,6 +121,8 @@ struct hg_grid {
     double* red;    // reduction scratch
     long long red_elems;
     double* dres;   // small device result buffer
+    double* dsum;   // sum(rho) of the last density, written on the device by the source preparation
+    int mass_pending;  // mass / rho_bar below not yet read back from dsum
     double* staging;  // dense nz*ny*nx doubles, allocated on first host transfer
     double Q[hg::kMaxQ];
     int have_Q;
@@ -140,6 +142,14 @@ struct hg_grid {
     // carries lambda, and the running sum of lambda over the reverse sub-steps (float pair or double, padded layout)
     hg_grid* adj;
     void* acc[2];
+    // host I/O pipeline (hg_io_step): an upload and a download stream, two slots of device buffers and, per slot,
+    // events for "density uploaded", "density consumed", "acceleration written", "acceleration downloaded"
+    cudaStream_t io_up, io_down;
+    void* io_rho[2];
+    void* io_acc[2];
+    size_t io_rho_bytes, io_acc_bytes;
+    cudaEvent_t io_ev[2][4];
+    long long io_issued, io_waited;
 };
 
 namespace hg {
@@ -168,11 +178,12 @@ int adjoint_gradient(hg_grid* a, const void* acc_a, const void* acc_b, void* out
 int launch_periodic_fill(hg_grid* g, int b);         // periodic ghosts of time-level buffer b
 int launch_temporal(hg_grid* g, int k);              // k fused sub-steps: cur -> 1-cur (temporal.cu)
 int ensure_staging(hg_grid* g);
-int prepare_source(hg_grid* g, const void* src, int dtype, double* sum_host);  // dense rho -> stored s
+int prepare_source(hg_grid* g, const void* src, int dtype);  // dense rho -> stored s, sum(rho) -> dsum (no sync)
+int sync_mass(hg_grid* g);                           // dsum -> host mass / rho_bar (syncs once per density)
 int set_ghosts_dirichlet(hg_grid* g);                // multipole data into both buffers
 int compute_moments(hg_grid* g, const void* rho_dense, int dtype);
 int seed_ghosts(hg_grid* g);                         // after hg_set_phi
-int reduce_sum(hg_grid* g, const void* dense, int dtype, double* out_host);
+int reduce_sum(hg_grid* g, const void* dense, int dtype, double* out_dev);
 int stats(hg_grid* g, hg_stats* s);
 int compare(hg_grid* g, const double* phiP_dense, double out[3]);
 int accel(hg_grid* g, void* ax, void* ay, void* az, int dtype);

@@ -38,6 +38,8 @@ REPORT_METRICS = [
 
 
 def short(name: str) -> str:
+    for ns in ("(anonymous namespace)::", "<unnamed>::", "unnamed>::", "hg::"):
+        name = name.replace(ns, "")
     return name.split("(")[0].replace("void ", "").strip()
 
 

@@ -1,0 +1,117 @@
+"""The pipelined host I/O step (hg_io_step / hg_io_wait) and the sync-free density upload: results bit-identical
+to the synchronous calls (set_density, step, accel, copy back) for every precision and boundary condition, the
+mass read back lazily, and the argument checks."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1602_05700_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+import paper_1602_05700_gb300 as hg  # noqa: E402
+
+CASES = [(40, "f32k", "robin", np.float32), (33, "f64", "robin", np.float64), (36, "f32k", "periodic", np.float64),
+         (28, "f64", "multipole", np.float32), (45, "f32k", "dirichlet", np.float32)]
+
+
+def densities(n, k, seed, dtype):
+    return [I.blob_density(n, I.draw_blobs(2 + s % 3, seed + s)).astype(dtype) for s in range(k)]
+
+
+@pytest.mark.parametrize("n,prec,bc,dt", CASES)
+def test_io_step_equals_synchronous_calls(n, prec, bc, dt):
+    lmax = 3 if bc == "multipole" else 0
+    a = hg.Grid.unit_cube(n, precision=prec, bc=bc, lmax=lmax)
+    b = hg.Grid.unit_cube(n, precision=prec, bc=bc, lmax=lmax)
+    rhos = densities(n, 5, 300 + n, dt)
+    adt = np.float64 if prec == "f64" else np.float32
+    outs = [[np.empty((n, n, n), adt) for _ in range(3)] for _ in range(2)]
+    want = []
+    for s, rho in enumerate(rhos):
+        a.io_step(rho, 7, outs[s % 2])
+        a.io_wait(1)
+        if s > 0:  # the previous step is complete: check its output now, before its buffers are reused
+            for x, y in zip(outs[(s - 1) % 2], want[s - 1]):
+                assert np.array_equal(x, y), f"step {s - 1}"
+        b.set_density(torch.from_numpy(rho).cuda())
+        b.step(7)
+        want.append([t.cpu().numpy() for t in b.accel(dtype=torch.float64 if prec == "f64" else torch.float32)])
+    a.io_wait(0)
+    for x, y in zip(outs[(len(rhos) - 1) % 2], want[-1]):
+        assert np.array_equal(x, y)
+    assert np.array_equal(a.phi_ghosted(), b.phi_ghosted())
+    sa, sb = a.stats(), b.stats()
+    assert sa["step"] == sb["step"] == 35
+    assert sa["mass"] == sb["mass"]
+
+
+def test_io_step_without_density_or_output():
+    n = 32
+    a = hg.Grid.unit_cube(n)
+    b = hg.Grid.unit_cube(n)
+    rho = densities(n, 1, 7, np.float32)[0]
+    out = [torch.empty((n, n, n), dtype=torch.float32).pin_memory() for _ in range(3)]
+    a.io_step(rho, 5)          # density in, no output
+    a.io_step(None, 6, out)    # source unchanged, output only
+    a.io_step(None, 4)         # neither
+    a.io_wait(0)
+    b.set_density(torch.from_numpy(rho).cuda())
+    b.step(11)
+    ref = b.accel()
+    b.step(4)
+    for x, y in zip(out, ref):
+        assert torch.equal(x, y.cpu())
+    assert np.array_equal(a.phi_ghosted(), b.phi_ghosted())
+
+
+@pytest.mark.parametrize("bc", ["robin", "periodic"])
+def test_device_density_mass_read_lazily(bc):
+    n = 24
+    g = hg.Grid.unit_cube(n, precision="f64", bc=bc)
+    og = O.unit_cube(n, 1.0, 1.0, 0.5, O.BC_ROBIN if bc == "robin" else O.BC_PERIODIC)
+    for s in range(3):
+        rho = densities(n, 1, 40 + s, np.float64)[0]
+        t = torch.from_numpy(rho).cuda()
+        g.set_density(t)
+        t.zero_()  # same stream: runs after the source preparation has read it
+        g.step(3)
+        assert abs(g.stats()["mass"] - O.mass(og, rho)) < 1e-13
+
+
+def test_density_buffer_reuse_is_stream_ordered():
+    n = 40
+    a = hg.Grid.unit_cube(n, bc="periodic")
+    b = hg.Grid.unit_cube(n, bc="periodic")
+    r1, r2 = densities(n, 2, 90, np.float32)
+    t = torch.from_numpy(r1).cuda()
+    a.set_density(t)
+    t.copy_(torch.from_numpy(r2).cuda())  # overwritten right after the call returns
+    a.step(9)
+    b.set_density(torch.from_numpy(r1).cuda())
+    b.step(9)
+    assert np.array_equal(a.phi_ghosted(), b.phi_ghosted())
+
+
+def test_io_step_rejects_bad_input():
+    n = 16
+    g = hg.Grid.unit_cube(n)
+    rho = np.zeros((n, n, n), np.float32)
+    with pytest.raises(hg.HGError):
+        g.io_step(torch.zeros((n, n, n), device="cuda"), 1)
+    with pytest.raises(hg.HGError):
+        g.io_step(rho, 1, [np.empty((n, n, n), np.float32)] * 2)
+    with pytest.raises(hg.HGError):
+        g.io_step(rho, 1, [np.empty((n, n, n), np.float32), np.empty((n, n, n), np.float32),
+                           np.empty((n, n, n), np.float64)])
+    with pytest.raises(hg.HGError):
+        g.io_step(rho, 1, [np.empty((n, n, n + 1), np.float32)] * 3)
+    with pytest.raises(hg.HGError):
+        g.io_wait(-1)
+    g.io_step(rho, 2, [np.empty((n, n, n), np.float32) for _ in range(3)])
+    g.io_wait(0)
+    assert g.stats()["step"] == 2
