@@ -33,8 +33,9 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 N_SUB = 20
-BYTES_PER_CELL = {"f32k": 28, "f64": 32}  # algorithmic HBM bytes of one sub-step (read 4 / write 3; read 3 / write 1)
-DP_OPS_PER_CELL = 15                      # FP64 instructions of the f64 update (cell.cuh)
+BYTES_PER_CELL = {"f32k": 24, "f64": 32}  # algorithmic HBM bytes of one sub-step: f32k read hi 4, lo code 2, dlt 4, s 4
+#                                          and write hi 4, lo 2, dlt 4; f64 read phi^n, phi^{n-1}, s, write phi^{n+1}
+DP_OPS_PER_CELL = 16                      # FP64 instructions of the f64 update (cell.cuh: 11 for L, 5 more)
 FP64_NOMINAL_TFLOPS = 1.25                # GB300 FP64 (FMA = 2 flops): 0.625 T instructions/s
 FALLBACK_HBM_GBS = 6800.0
 
@@ -202,7 +203,7 @@ def run_ours(args, rank, world, local_rank):
         subs = N_SUB * r["steps"] / max(r["kern_n"], 1)  # sub-steps per launch (the temporal depth)
         alg = BYTES_PER_CELL["f32k"] * cells  # one read of the state and one write per launch
         ach = alg / (avg * 1e-3) / 1e9
-        kname = "k_step_f32k" if r["depth"] == 1 else f"k_temporal_f32k<{r['depth']}>"
+        kname = "k_step_f32k_tma" if r["depth"] == 1 else f"k_temporal_f32k<{r['depth']}>"
         return {"bound": "hbm", "achieved": round(ach, 1), "peak": hbm_peak, "unit": "GB/s",
                 "frac": round(ach / hbm_peak, 4), "peak_kind": f"{peak_kind} copy bandwidth",
                 "traffic": stencil_traffic(kname, n), "kernel": kname, "alg_bytes_per_launch": alg,
@@ -234,7 +235,8 @@ def run_ours(args, rank, world, local_rank):
                    "precision": "f32 compensated (Kahan)" if args.prec == "f32k" else "f64",
                    "temporal_depth": best, "depth_sweep_gcells": sweep,
                    "parallelism": f"{world} independent grids (one per GPU)",
-                   "l2": f"working set {6 * 4 * cells / 1e9:.1f} GB per grid >> 129 MB L2 (no flush needed)"},
+                   "l2": f"working set {20 * cells / 1e9:.1f} GB per grid (hi, lo codes, dlt, s) >> 129 MB L2 "
+                         "(no flush needed)"},
         "roofline": roofline(res),
         "gpu_launches": res["launches"],
         "clocks": res["clocks"],
@@ -265,15 +267,15 @@ def run_ours(args, rank, world, local_rank):
     if not args.skip_e2e:
         ke, we = max(4, min(steps, 10)), 2
         host_rho = [rhos[s % len(rhos)].cpu().pin_memory() for s in range(we + ke)]
-        host_acc = [[torch.empty((n, n, n), dtype=torch.float32).pin_memory() for _ in range(3)] for _ in range(2)]
+        host_acc = [[torch.empty((n, n, n), dtype=torch.float32).pin_memory() for _ in range(3)] for _ in range(3)]
         g = hg.Grid(n, n, n, W["h"], W["origin"], W["c"], W["G"], W["dt"], "f32k", "robin")
         if best > 1:
             g.set_temporal_depth(best)
 
         def e2e_steps(first, count):
             for s in range(first, first + count):
-                g.io_step(host_rho[s], N_SUB, host_acc[s % 2])
-                g.io_wait(1)  # step s-1 is done: its outputs are on the host, its buffers free again
+                g.io_step(host_rho[s], N_SUB, host_acc[s % 3])
+                g.io_wait(2)  # step s-2 is done: its outputs are on the host, its buffers free again
             g.io_wait(0)
 
         e2e_steps(0, we)
@@ -287,7 +289,8 @@ def run_ours(args, rank, world, local_rank):
                        "h2d_bytes_per_step": 4 * cells, "d2h_bytes_per_step": 12 * cells, "steps": ke,
                        "temporal_depth": best,
                        "note": "each step: its density from pinned host memory in, -grad phi (3 x f32) out to "
-                               "pinned host memory; copies overlap the neighbouring steps' sub-steps"}
+                               "pinned host memory; two steps in flight, so the copies overlap the neighbouring steps' "
+                               "sub-steps"}
     if rank == 0 and not args.skip_cpu:
         line["cpu_baseline"] = cpu_baseline(args.n, args.cpu_substeps)
     multi.finalize()

@@ -195,9 +195,10 @@ int hg_profile_read(hg_grid* g, double* substep_kernel_ms, long long* substep_la
  *   hg_set_density from that slot, n_substeps sub-steps (hg_step), -grad phi (hg_accel, central differences) into
  *   a device slot, and its copy to ax_host, ay_host, az_host (nz*ny*nx values of acc_dtype each) on a download
  *   stream of the grid.
- * Two slots alternate, so the upload of call s+1 and the download of call s overlap the sub-steps of the other
- * call; the grid's stream waits only on the upload it consumes, and a slot is refilled only after its previous
- * contents have been used.  rho_host may be NULL (the source is unchanged) and the three acceleration pointers
+ * Two device slots alternate, and the grid's stream waits only on the upload it consumes; a slot is refilled only
+ * after its previous contents have been used (ordered by events, not by the host).  With two calls in flight
+ * (hg_io_wait(g, 2) after each call) the upload of call s+1 and the download of call s-1 both run under the
+ * sub-steps of call s.  rho_host may be NULL (the source is unchanged) and the three acceleration pointers
  * may all be NULL (no output).  The host buffers must be page-locked for the copies to overlap (pageable memory
  * works, synchronously) and belong to the library until hg_io_wait has covered the call.  Device memory: two
  * density slots and two acceleration slots, allocated on first use.  Errors: HG_ERR_ARG (bad dtype, only some

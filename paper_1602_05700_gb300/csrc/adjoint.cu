@@ -14,6 +14,7 @@
 //
 // Kernels here: add an injection into the shadow state, accumulate sum_m lambda^m (float pairs for the compensated
 // precision, double for FP64), and turn the sum into the gradient.
+#include "cell.cuh"
 #include "hg_internal.cuh"
 
 namespace hg {
@@ -46,13 +47,15 @@ __global__ void k_inject(int prec, const void* v, int vdt, void* hi, void* lo, v
             ((double*)hi)[q] += x;
         } else {
             float* h = (float*)hi;
-            float* l = (float*)lo;
+            lo_t* l = (lo_t*)lo;
             const float xh = (float)x, xl = (float)(x - (double)xh);
+            const float h0 = h[q];
             float s, e;
-            two_sum(h[q], xh, s, e);
-            const float t = (l[q] + xl) + e;
-            h[q] = s + t;
-            l[q] = t - (h[q] - s);
+            two_sum(h0, xh, s, e);
+            const float t = (lo_decode(h0, l[q]) + xl) + e;
+            const float hn = s + t;
+            h[q] = hn;
+            l[q] = lo_encode(hn, t - (hn - s));
             ((float*)dlt)[q] += xh;
         }
     });
@@ -67,8 +70,9 @@ __global__ void k_accumulate(int prec, const void* hi, const void* lo, void* acc
             float* a = (float*)acc_a;
             float* b = (float*)acc_b;
             float s, e;
-            two_sum(a[q], ((const float*)hi)[q], s, e);
-            const float t = b[q] + (e + ((const float*)lo)[q]);
+            const float h = ((const float*)hi)[q];
+            two_sum(a[q], h, s, e);
+            const float t = b[q] + (e + lo_decode(h, ((const lo_t*)lo)[q]));
             a[q] = s + t;
             b[q] = t - (a[q] - s);
         }

@@ -151,12 +151,13 @@ __device__ __forceinline__ void put_ghost(int prec, void* p0, void* p1, void* l0
         ((double*)p0)[q] = v;
         ((double*)p1)[q] = v;
     } else {
-        float hi, lo;
+        float hi;
+        lo_t lo;
         split_f32(v, hi, lo);
         ((float*)p0)[q] = hi;
         ((float*)p1)[q] = hi;
-        ((float*)l0)[q] = lo;
-        ((float*)l1)[q] = lo;
+        ((lo_t*)l0)[q] = lo;
+        ((lo_t*)l1)[q] = lo;
     }
 }
 
@@ -173,16 +174,17 @@ __global__ void k_dirichlet(int prec, void* p0, void* p1, void* l0, void* l1, La
 
 __device__ __forceinline__ double read_phi(int prec, const void* p, const void* lo, long long q) {
     if (prec == HG_PREC_F64) return ((const double*)p)[q];
-    return join_f32(((const float*)p)[q], ((const float*)lo)[q]);
+    return join_f32(((const float*)p)[q], ((const lo_t*)lo)[q]);
 }
 __device__ __forceinline__ void write_phi(int prec, void* p, void* lo, long long q, double v) {
     if (prec == HG_PREC_F64) {
         ((double*)p)[q] = v;
     } else {
-        float hi, l;
+        float hi;
+        lo_t l;
         split_f32(v, hi, l);
         ((float*)p)[q] = hi;
-        ((float*)lo)[q] = l;
+        ((lo_t*)lo)[q] = l;
     }
 }
 
@@ -208,7 +210,7 @@ __device__ __forceinline__ void periodic_ghost(int prec, void* p, void* lo, cons
         ((double*)p)[qg] = ((const double*)p)[qs];
     } else {
         ((float*)p)[qg] = ((const float*)p)[qs];
-        ((float*)lo)[qg] = ((const float*)lo)[qs];
+        ((lo_t*)lo)[qg] = ((const lo_t*)lo)[qs];
     }
 }
 

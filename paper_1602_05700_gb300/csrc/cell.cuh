@@ -8,9 +8,51 @@
 // accumulates in its slow modes (about 3e-12 relative after 2000 sub-steps at 64^3 against ~3e-14).
 #pragma once
 
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 namespace hg {
+
+// ---- storage of the compensation -------------------------------------------------------------------------------
+// The compensated state keeps phi^n = hi + lo with |lo| <= ulp(hi)/2 (lo is the exact rounding error of the
+// Fast2Sum that produced hi).  lo is stored in 16 bits as the half-precision number f = 2^24 lo / hi, |f| <= 1, and
+// read back as lo = hi (f 2^-24).  The code keeps 11 significant bits of lo, so phi is held to about 2^-36 |phi|
+// (36 bits) instead of 48 -- far below the other float roundings of the sub-step (the FP32 source and increment),
+// which set the accuracy -- for 2 bytes per cell instead of 4.  Every reader decodes a stored code to the same
+// float (one rounded product), so all kernels see one and the same state.
+using lo_t = __half;
+
+__device__ __forceinline__ float lo_decode(float hi, lo_t f) {
+    return __fmul_rn(hi, __fmul_rn(__half2float(f), 5.9604644775390625e-8f));  // f * 2^-24 is exact
+}
+
+// f = 2^24 lo / hi by the approximate reciprocal (the code only has to be decoded consistently); lo = 0 whenever
+// hi = 0 (a Fast2Sum with a zero sum has a zero error), which the select keeps away from 0 * inf
+__device__ __forceinline__ lo_t lo_encode(float hi, float lo) {
+    const float f = lo == 0.f ? 0.f : __fdividef(__fmul_rn(lo, 16777216.f), hi);
+    return __float2half_rn(f);
+}
+
+// the value of lo after a store and a load (temporally blocked levels that never pass through memory use it to
+// round exactly like the single sweep)
+__device__ __forceinline__ float lo_round(float hi, float lo) { return lo_decode(hi, lo_encode(hi, lo)); }
+
+// four consecutive codes as one 8-byte word
+__device__ __forceinline__ float4 lo_decode4(const float4& hi, uint2 raw) {
+    const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&raw.x));
+    const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&raw.y));
+    const float k = 5.9604644775390625e-8f;
+    return make_float4(__fmul_rn(hi.x, __fmul_rn(a.x, k)), __fmul_rn(hi.y, __fmul_rn(a.y, k)),
+                       __fmul_rn(hi.z, __fmul_rn(b.x, k)), __fmul_rn(hi.w, __fmul_rn(b.y, k)));
+}
+__device__ __forceinline__ uint2 lo_encode4(const float4& hi, const float4& lo) {
+    const lo_t c0 = lo_encode(hi.x, lo.x), c1 = lo_encode(hi.y, lo.y), c2 = lo_encode(hi.z, lo.z),
+               c3 = lo_encode(hi.w, lo.w);
+    uint2 r;
+    r.x = (unsigned)__half_as_ushort(c0) | ((unsigned)__half_as_ushort(c1) << 16);
+    r.y = (unsigned)__half_as_ushort(c2) | ((unsigned)__half_as_ushort(c3) << 16);
+    return r;
+}
 
 // f32 with compensated increments: phi^n = hi + lo, d = phi^n - phi^{n-1}.
 //   L  = sum(hi_nb - hi) + sum(lo_nb) - 6 lo          (neighbour order -x, +x, -y, +y, -z, +z)
@@ -76,11 +118,13 @@ __device__ __forceinline__ void robin_update_f32k(float a, float b, float hg, fl
     lo_o = __fsub_rn(t, __fsub_rn(hi_o, s));
 }
 
-// a double as a float and its rounding remainder
-__device__ __forceinline__ void split_f32(double v, float& hi, float& lo) {
+// a double as a float and the code of its rounding remainder, and back
+__device__ __forceinline__ void split_f32(double v, float& hi, lo_t& lo) {
     hi = __double2float_rn(v);
-    lo = __double2float_rn(__dsub_rn(v, (double)hi));
+    lo = lo_encode(hi, __double2float_rn(__dsub_rn(v, (double)hi)));
 }
-__device__ __forceinline__ double join_f32(float hi, float lo) { return __dadd_rn((double)hi, (double)lo); }
+__device__ __forceinline__ double join_f32(float hi, lo_t lo) {
+    return __dadd_rn((double)hi, (double)lo_decode(hi, lo));
+}
 
 }  // namespace hg

@@ -2,9 +2,12 @@
 // -grad phi (arXiv 1602.05700: the force the hydro step consumes, Sec. 2), and the FP64 diagnostics of Sec. 4
 // (Eq. error) and of the steady state (Eq. Poissoneq.).  Reductions are deterministic: fixed grid, per-block
 // partial sums, one finishing block.
+#include "cell.cuh"
 #include "hg_internal.cuh"
 
 namespace hg {
+
+static_assert(sizeof(lo_t) == sizeof(lo_code), "the compensation code is 16 bits wide");
 
 namespace {
 
@@ -21,10 +24,10 @@ __device__ __forceinline__ void st(void* p, int dtype, long long i, double v) {
         ((float*)p)[i] = (float)v;
 }
 
-// value of phi^n at padded index q, in double (F32K: float plus its compensation)
+// value of phi^n at padded index q, in double (F32K: float plus its decoded compensation)
 __device__ __forceinline__ double phi_at(int prec, const void* p, const void* lo, long long q) {
     if (prec == HG_PREC_F64) return ((const double*)p)[q];
-    return (double)((const float*)p)[q] + (double)((const float*)lo)[q];
+    return join_f32(((const float*)p)[q], ((const lo_t*)lo)[q]);
 }
 
 // visit every interior cell: blocks stride over the rows (j, k), threads over x (coalesced, no per-cell division)
@@ -60,12 +63,17 @@ __global__ void __launch_bounds__(kThreads) k_pack(const TS* __restrict__ src, T
     const float scale32 = (float)scale, shift32 = (float)shift;
     if constexpr (sizeof(TS) == 4 && sizeof(TD) == 4) {
         if ((L.nx & 3) == 0 && ((uintptr_t)src & 15) == 0) {  // 16-byte groups on both sides
+            // a block takes rpb rows at a time (all its threads busy when a row has fewer groups than threads)
             const long long rows = (long long)L.ny * L.nz;
-            for (long long row = blockIdx.x; row < rows; row += gridDim.x) {
+            const int gpr = L.nx >> 2, rpb = gpr >= (int)blockDim.x ? 1 : (int)blockDim.x / gpr;
+            const int sub = rpb == 1 ? 0 : (int)threadIdx.x / gpr, i0 = rpb == 1 ? (int)threadIdx.x : (int)threadIdx.x % gpr;
+            const int istep = rpb == 1 ? (int)blockDim.x : gpr;
+            for (long long row = (long long)blockIdx.x * rpb + sub; row < rows; row += (long long)gridDim.x * rpb) {
+                if (sub >= rpb) break;  // threads beyond rpb * gpr
                 const int j = (int)(row % L.ny), k = (int)(row / L.ny);
                 const float4* s4 = reinterpret_cast<const float4*>(src + row * L.nx);
                 float4* d4 = reinterpret_cast<float4*>(dst + L.at(0, j, k));
-                for (int i = threadIdx.x; i < (L.nx >> 2); i += blockDim.x) {
+                for (int i = i0; i < gpr; i += istep) {
                     const float4 x = __ldg(s4 + i);
                     d4[i] = make_float4(scale32 * (x.x - shift32), scale32 * (x.y - shift32), scale32 * (x.z - shift32),
                                         scale32 * (x.w - shift32));
@@ -132,11 +140,14 @@ __global__ void k_seed(int prec, const void* phi, const void* prev, int sdt, voi
             ((double*)p_cur)[q] = a;
             ((double*)p_oth)[q] = b;
         } else {
-            const float ha = (float)a, hb = (float)b;
+            float ha, hb;
+            lo_t la, lb;
+            split_f32(a, ha, la);
+            split_f32(b, hb, lb);
             ((float*)p_cur)[q] = ha;
-            ((float*)l_cur)[q] = (float)(a - (double)ha);
+            ((lo_t*)l_cur)[q] = la;
             ((float*)p_oth)[q] = hb;
-            ((float*)l_oth)[q] = (float)(b - (double)hb);
+            ((lo_t*)l_oth)[q] = lb;
             ((float*)dlt)[q] = (float)(a - b);
         }
     });
@@ -150,11 +161,12 @@ __global__ void k_accel(int prec, const void* p, const void* lo, void* ax, void*
         const long long q = L.at(i, j, k);
         if (prec == HG_PREC_F32K && ddt == HG_DT_F32) {
             const float* h = (const float*)p;
-            const float* l = (const float*)lo;
+            const lo_t* lc = (const lo_t*)lo;
+            auto l = [&](long long u) { return lo_decode(h[u], lc[u]); };
             const float s = (float)inv2h;
-            ((float*)ax)[c] = -((h[q + 1] - h[q - 1]) + (l[q + 1] - l[q - 1])) * s;
-            ((float*)ay)[c] = -((h[q + L.pitch] - h[q - L.pitch]) + (l[q + L.pitch] - l[q - L.pitch])) * s;
-            ((float*)az)[c] = -((h[q + L.plane] - h[q - L.plane]) + (l[q + L.plane] - l[q - L.plane])) * s;
+            ((float*)ax)[c] = -((h[q + 1] - h[q - 1]) + (l(q + 1) - l(q - 1))) * s;
+            ((float*)ay)[c] = -((h[q + L.pitch] - h[q - L.pitch]) + (l(q + L.pitch) - l(q - L.pitch))) * s;
+            ((float*)az)[c] = -((h[q + L.plane] - h[q - L.plane]) + (l(q + L.plane) - l(q - L.plane))) * s;
         } else {
             st(ax, ddt, c, -(phi_at(prec, p, lo, q + 1) - phi_at(prec, p, lo, q - 1)) * inv2h);
             st(ay, ddt, c, -(phi_at(prec, p, lo, q + L.pitch) - phi_at(prec, p, lo, q - L.pitch)) * inv2h);
@@ -165,9 +177,9 @@ __global__ void k_accel(int prec, const void* p, const void* lo, void* ax, void*
 
 // Vectorised -grad phi for compensated float grids with float output (the per-hydro-step call): the work mapping
 // of the sub-step kernel (a warp per 128-cell x-row, float4 per lane, x neighbours by shuffles, a z register queue)
-// and the same arithmetic as k_accel.  HBM bytes per cell: read hi, lo; write ax, ay, az = 20 B.
+// and the same arithmetic as k_accel.  HBM bytes per cell: read hi 4, lo 2; write ax, ay, az 12 = 18 B.
 constexpr int kAccWY = 8;
-__global__ void __launch_bounds__(32 * kAccWY) k_accel_f32k(const float* __restrict__ hi, const float* __restrict__ lo,
+__global__ void __launch_bounds__(32 * kAccWY) k_accel_f32k(const float* __restrict__ hi, const lo_t* __restrict__ lo,
                                                             float* __restrict__ ax, float* __restrict__ ay,
                                                             float* __restrict__ az, Layout L, float s, int zb) {
     const int lane = threadIdx.x;
@@ -178,34 +190,35 @@ __global__ void __launch_bounds__(32 * kAccWY) k_accel_f32k(const float* __restr
     const bool vec = (L.nx & 3) == 0 && i0 + 3 < L.nx;
     const int k0 = blockIdx.z * zb, k1 = min(L.nz, k0 + zb);
     auto ld4 = [](const float* p) { return __ldg(reinterpret_cast<const float4*>(p)); };
+    auto ldl4 = [](const lo_t* p) { return __ldg(reinterpret_cast<const uint2*>(p)); };
     const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
     long long q = L.at(i0, j, k0);
     float4 hm = z4, hc = z4, lm = z4, lc = z4;
     if (halo) {
         hm = ld4(hi + q - L.plane);
-        lm = ld4(lo + q - L.plane);
+        lm = lo_decode4(hm, ldl4(lo + q - L.plane));
         hc = ld4(hi + q);
-        lc = ld4(lo + q);
+        lc = lo_decode4(hc, ldl4(lo + q));
     }
     for (int k = k0; k < k1; ++k, q += L.plane) {
         float4 hp = z4, lp = z4, hs = z4, hn = z4, ls = z4, ln = z4;
         float hl = 0.f, hr = 0.f, ll = 0.f, lr = 0.f;
         if (halo) {
             hp = ld4(hi + q + L.plane);
-            lp = ld4(lo + q + L.plane);
+            lp = lo_decode4(hp, ldl4(lo + q + L.plane));
         }
         if (active) {
             hs = ld4(hi + q - L.pitch);
             hn = ld4(hi + q + L.pitch);
-            ls = ld4(lo + q - L.pitch);
-            ln = ld4(lo + q + L.pitch);
+            ls = lo_decode4(hs, ldl4(lo + q - L.pitch));
+            ln = lo_decode4(hn, ldl4(lo + q + L.pitch));
             if (lane == 0) {
                 hl = __ldg(hi + q - 1);
-                ll = __ldg(lo + q - 1);
+                ll = lo_decode(hl, lo[q - 1]);
             }
             if (lane == 31 && i0 + 4 <= L.nx) {
                 hr = __ldg(hi + q + 4);
-                lr = __ldg(lo + q + 4);
+                lr = lo_decode(hr, lo[q + 4]);
             }
         }
         const float shl = __shfl_up_sync(0xffffffffu, hc.w, 1), sll = __shfl_up_sync(0xffffffffu, lc.w, 1);
@@ -443,7 +456,7 @@ int accel(hg_grid* g, void* ax, void* ay, void* az, int dtype) {
     if (g->prec == HG_PREC_F32K && dtype == HG_DT_F32 && aligned) {
         const int zb = g->nz < 32 ? g->nz : 32;
         dim3 block(32, kAccWY), grid((g->nx + 127) / 128, (g->ny + kAccWY - 1) / kAccWY, (g->nz + zb - 1) / zb);
-        k_accel_f32k<<<grid, block, 0, g->stream>>>((const float*)g->phi[g->cur], (const float*)g->lo[g->cur],
+        k_accel_f32k<<<grid, block, 0, g->stream>>>((const float*)g->phi[g->cur], (const lo_t*)g->lo[g->cur],
                                                     (float*)ax, (float*)ay, (float*)az, g->L,
                                                     (float)(1.0 / (2.0 * g->h)), zb);
     } else {
@@ -457,6 +470,7 @@ int accel(hg_grid* g, void* ax, void* ay, void* az, int dtype) {
 int stats(hg_grid* g, hg_stats* s) {
     int rc = sync_mass(g);
     if (rc) return rc;
+    if ((rc = device_error(g))) return rc;
     k_stats<<<kRedBlocks, kThreads, 0, g->stream>>>(g->prec, g->phi[g->cur], g->lo[g->cur], g->phi[1 - g->cur],
                                                     g->dlt[g->dcur], g->rho, g->L, 1.0 / (g->h * g->h),
                                                     1.0 / ((g->c * g->dt) * (g->c * g->dt)), g->red);

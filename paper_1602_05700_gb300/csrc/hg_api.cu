@@ -106,12 +106,24 @@ static void release(hg_grid* g) {
     for (auto& slot : g->io_ev)
         for (cudaEvent_t ev : slot)
             if (ev) cudaEventDestroy(ev);
+    for (cudaEvent_t ev : g->io_done)
+        if (ev) cudaEventDestroy(ev);
     if (g->io_up) cudaStreamDestroy(g->io_up);
     if (g->io_down) cudaStreamDestroy(g->io_down);
     if (g->prof_ev) {
         for (int e = 0; e < 2 * kProfPairs; ++e) cudaEventDestroy(g->prof_ev[e]);
         delete[] g->prof_ev;
     }
+}
+
+int device_error(hg_grid* g) {
+    int e = 0;
+    HG_CUDA(cudaMemcpyAsync(&e, g->derr, sizeof e, cudaMemcpyDeviceToHost, g->stream));
+    HG_CUDA(cudaStreamSynchronize(g->stream));
+    if (!e) return HG_OK;
+    HG_CUDA(cudaMemsetAsync(g->derr, 0, sizeof e, g->stream));
+    return fail(HG_ERR_TIMEOUT, "a bounded wait inside a sub-step kernel gave up (the results of that launch are "
+                                "not valid)");
 }
 
 int prof_fold(hg_grid* g) {
@@ -218,32 +230,34 @@ int hg_init_grid(hg_grid** out, int nx, int ny, int nz, double h, const double o
         }
     }
     if (rc == HG_OK && bc == HG_BC_ROBIN) rc = build_robin(g);
-    size_t bytes = (size_t)g->L.elems * g->esize;
-    auto alloc = [&](void** p) {
+    const size_t bytes = (size_t)g->L.elems * g->esize;
+    const size_t lo_bytes = (size_t)g->L.elems * sizeof(hg::lo_code);
+    auto alloc = [&](void** p, size_t nb) {
         if (rc != HG_OK) return;
-        cudaError_t e2 = cudaMalloc(p, bytes);
+        cudaError_t e2 = cudaMalloc(p, nb);
         if (e2 != cudaSuccess) {
             rc = cuda_fail(e2, "cudaMalloc(state)");
             return;
         }
-        e2 = cudaMemsetAsync(*p, 0, bytes, g->stream);
+        e2 = cudaMemsetAsync(*p, 0, nb, g->stream);
         if (e2 != cudaSuccess) rc = cuda_fail(e2, "cudaMemsetAsync(state)");
     };
-    alloc(&g->phi[0]);
-    alloc(&g->phi[1]);
-    alloc(&g->rho);
+    alloc(&g->phi[0], bytes);
+    alloc(&g->phi[1], bytes);
+    alloc(&g->rho, bytes);
     if (precision == HG_PREC_F32K) {
-        alloc(&g->lo[0]);
-        alloc(&g->lo[1]);
-        alloc(&g->dlt[0]);
+        alloc(&g->lo[0], lo_bytes);  // 16-bit codes of the compensation
+        alloc(&g->lo[1], lo_bytes);
+        alloc(&g->dlt[0], bytes);
     }
     if (rc == HG_OK) {
         g->red_elems = reduction_scratch_elems();
         e = cudaMalloc(&g->red, (size_t)g->red_elems * sizeof(double));
-        if (e == cudaSuccess) e = cudaMalloc(&g->dres, (kMaxQ + 1) * sizeof(double));
-        if (e == cudaSuccess) e = cudaMemsetAsync(g->dres, 0, (kMaxQ + 1) * sizeof(double), g->stream);
+        if (e == cudaSuccess) e = cudaMalloc(&g->dres, (kMaxQ + 2) * sizeof(double));
+        if (e == cudaSuccess) e = cudaMemsetAsync(g->dres, 0, (kMaxQ + 2) * sizeof(double), g->stream);
         if (e != cudaSuccess) rc = cuda_fail(e, "cudaMalloc(reduction scratch)");
         g->dsum = g->dres + kMaxQ;
+        g->derr = (int*)(g->dres + kMaxQ + 1);
     }
     if (rc == HG_OK) {
         e = cudaStreamSynchronize(g->stream);
@@ -440,10 +454,15 @@ static void** buffer(hg_grid* g, int b) {
     void** all[6] = {&g->phi[0], &g->phi[1], &g->rho, &g->lo[0], &g->lo[1], &g->dlt[g->dcur]};
     return all[b];
 }
+static size_t buffer_bytes(const hg_grid* g, int b) {
+    return (size_t)g->L.elems * (b == 3 || b == 4 ? sizeof(lo_code) : (size_t)g->esize);
+}
 
 size_t hg_state_bytes(const hg_grid* g) {
     if (!g) return 0;
-    return sizeof(StateHeader) + (size_t)n_buffers(g) * (size_t)g->L.elems * g->esize;
+    size_t n = sizeof(StateHeader);
+    for (int b = 0; b < n_buffers(g); ++b) n += buffer_bytes(g, b);
+    return n;
 }
 
 int hg_save_state(hg_grid* g, void* buf, int on_device) {
@@ -472,8 +491,10 @@ int hg_save_state(hg_grid* g, void* buf, int on_device) {
     else
         memcpy(buf, &H, sizeof H);
     char* p = (char*)buf + sizeof H;
-    size_t bytes = (size_t)g->L.elems * g->esize;
-    for (int b = 0; b < n_buffers(g); ++b, p += bytes) HG_CUDA(cudaMemcpyAsync(p, *buffer(g, b), bytes, kind, g->stream));
+    for (int b = 0; b < n_buffers(g); ++b) {
+        HG_CUDA(cudaMemcpyAsync(p, *buffer(g, b), buffer_bytes(g, b), kind, g->stream));
+        p += buffer_bytes(g, b);
+    }
     HG_CUDA(cudaStreamSynchronize(g->stream));  // the header copy reads a stack variable
     return HG_OK;
 }
@@ -494,8 +515,10 @@ int hg_load_state(hg_grid* g, const void* buf, int on_device) {
         H.bc != g->bc || H.lmax != g->lmax)
         return fail(HG_ERR_ARG, "state buffer does not match this grid");
     const char* p = (const char*)buf + sizeof H;
-    size_t bytes = (size_t)g->L.elems * g->esize;
-    for (int b = 0; b < n_buffers(g); ++b, p += bytes) HG_CUDA(cudaMemcpyAsync(*buffer(g, b), p, bytes, kind, g->stream));
+    for (int b = 0; b < n_buffers(g); ++b) {
+        HG_CUDA(cudaMemcpyAsync(*buffer(g, b), p, buffer_bytes(g, b), kind, g->stream));
+        p += buffer_bytes(g, b);
+    }
     if (!on_device) HG_CUDA(cudaStreamSynchronize(g->stream));
     g->cur = H.cur;
     g->have_Q = H.have_Q;
@@ -547,10 +570,12 @@ int hg_adjoint_reset(hg_grid* g) {
         if (g->prec == HG_PREC_F32K) HG_CUDA(cudaMalloc(&g->acc[1], bytes));
     }
     hg_grid* a = g->adj;
-    const size_t bytes = (size_t)a->L.elems * a->esize;
-    void* bufs[] = {a->phi[0], a->phi[1], a->lo[0], a->lo[1], a->dlt[0], a->dlt[1], g->acc[0], g->acc[1]};
+    const size_t bytes = (size_t)a->L.elems * a->esize, lo_bytes = (size_t)a->L.elems * sizeof(lo_code);
+    void* bufs[] = {a->phi[0], a->phi[1], a->dlt[0], a->dlt[1], g->acc[0], g->acc[1]};
     for (void* b : bufs)
         if (b) HG_CUDA(cudaMemsetAsync(b, 0, bytes, g->stream));
+    for (void* b : {a->lo[0], a->lo[1]})
+        if (b) HG_CUDA(cudaMemsetAsync(b, 0, lo_bytes, g->stream));
     a->cur = 0;
     a->dcur = 0;
     a->step = 0;
@@ -618,6 +643,7 @@ static int io_ready(hg_grid* g, size_t rho_bytes, size_t acc_bytes) {
         HG_CUDA(cudaStreamCreateWithFlags(&g->io_down, cudaStreamNonBlocking));
         for (auto& slot : g->io_ev)
             for (cudaEvent_t& ev : slot) HG_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        for (cudaEvent_t& ev : g->io_done) HG_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
     }
     if (rho_bytes <= g->io_rho_bytes && acc_bytes <= g->io_acc_bytes) return HG_OK;
     // the slots grow (a wider dtype) only while nothing of the pipeline is in flight
@@ -661,7 +687,10 @@ int hg_io_step(hg_grid* g, const void* rho_host, int rho_dtype, int n_substeps, 
     const size_t comp = want_acc ? align_up(n * dt_size(acc_dtype), 256) : 0;  // one component, 256-byte aligned
     if ((rc = io_ready(g, rho_bytes, 3 * comp))) return rc;
     const int k = (int)(g->io_issued & 1);
-    cudaEvent_t* ev = g->io_ev[k];  // 0 uploaded, 1 consumed, 2 acceleration written, 3 step complete
+    cudaEvent_t* ev = g->io_ev[k];  // 0 uploaded, 1 consumed, 2 acceleration written
+    constexpr int kRing = (int)(sizeof g->io_done / sizeof g->io_done[0]);
+    cudaEvent_t done = g->io_done[g->io_issued % kRing];
+    cudaEvent_t prev_done = g->io_done[(g->io_issued + kRing - 2) % kRing];  // this slot's previous user, if any
     if (rho_host) {
         HG_CUDA(cudaStreamWaitEvent(g->io_up, ev[1], 0));  // the slot's previous density has been packed
         HG_CUDA(cudaMemcpyAsync(g->io_rho[k], rho_host, rho_bytes, cudaMemcpyHostToDevice, g->io_up));
@@ -673,7 +702,8 @@ int hg_io_step(hg_grid* g, const void* rho_host, int rho_dtype, int n_substeps, 
     if ((rc = hg_step(g, n_substeps))) return rc;
     char* a = (char*)g->io_acc[k];
     if (want_acc) {
-        HG_CUDA(cudaStreamWaitEvent(g->stream, ev[3], 0));  // the slot's previous acceleration has been downloaded
+        if (g->io_issued >= 2)  // the slot's previous acceleration has been downloaded
+            HG_CUDA(cudaStreamWaitEvent(g->stream, prev_done, 0));
         if ((rc = accel(g, a, a + comp, a + 2 * comp, acc_dtype))) return rc;
     }
     HG_CUDA(cudaEventRecord(ev[2], g->stream));
@@ -684,7 +714,7 @@ int hg_io_step(hg_grid* g, const void* rho_host, int rho_dtype, int n_substeps, 
         HG_CUDA(cudaMemcpyAsync(ay_host, a + comp, bytes, cudaMemcpyDeviceToHost, g->io_down));
         HG_CUDA(cudaMemcpyAsync(az_host, a + 2 * comp, bytes, cudaMemcpyDeviceToHost, g->io_down));
     }
-    HG_CUDA(cudaEventRecord(ev[3], g->io_down));
+    HG_CUDA(cudaEventRecord(done, g->io_down));
     ++g->io_issued;
     return HG_OK;
 }
@@ -693,10 +723,10 @@ int hg_io_wait(hg_grid* g, int keep) {
     int rc = check_grid(g);
     if (rc) return rc;
     if (keep < 0) return fail(HG_ERR_ARG, "keep must be >= 0");
-    // a slot's completion event is re-recorded two calls later, so waiting on it is exact for the last two calls
-    // and conservative (waits longer) for older ones
+    // completion events form a ring of 8: exact for the last 8 calls, conservative (waits longer) for older ones
+    constexpr int kRing = (int)(sizeof g->io_done / sizeof g->io_done[0]);
     while (g->io_waited < g->io_issued - keep) {
-        HG_CUDA(cudaEventSynchronize(g->io_ev[g->io_waited & 1][3]));
+        HG_CUDA(cudaEventSynchronize(g->io_done[g->io_waited % kRing]));
         ++g->io_waited;
     }
     return HG_OK;
@@ -706,6 +736,7 @@ int hg_sync(hg_grid* g) {
     int rc = check_grid(g);
     if (rc) return rc;
     HG_CUDA(cudaStreamSynchronize(g->stream));
+    if ((rc = device_error(g))) return rc;
     if (g->io_up) {
         HG_CUDA(cudaStreamSynchronize(g->io_up));
         HG_CUDA(cudaStreamSynchronize(g->io_down));

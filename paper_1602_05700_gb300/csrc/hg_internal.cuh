@@ -1,6 +1,7 @@
 // Internal definitions shared by the translation units of the CUDA library (not part of the C ABI).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -92,6 +93,9 @@ struct YlmNorm {
 };
 void fill_ylm_norms(YlmNorm& N);
 
+// storage unit of the compensation of a compensated-float state (a 16-bit code, decoded in cell.cuh)
+typedef unsigned short lo_code;
+
 // ---- the grid --------------------------------------------------------------------------------------------------
 }  // namespace hg
 
@@ -108,7 +112,8 @@ struct hg_grid {
     hg::Layout L;
     hg::Faces F;
     // state: F64 -> phi[cur] = phi^n, phi[1-cur] = phi^{n-1};
-    //        F32K -> phi[cur] (the float part) + lo[cur] (its compensation) = phi^n, dlt[dcur] = phi^n - phi^{n-1}
+    //        F32K -> phi[cur] (the float part) + lo[cur] (its compensation, 16-bit codes) = phi^n,
+    //                dlt[dcur] = phi^n - phi^{n-1}
     //        (dlt[1] exists once temporal blocking is enabled: fused sub-steps read neighbours' dlt, so it ping-pongs)
     void* phi[2];
     void* lo[2];
@@ -122,6 +127,7 @@ struct hg_grid {
     long long red_elems;
     double* dres;   // small device result buffer
     double* dsum;   // sum(rho) of the last density, written on the device by the source preparation
+    int* derr;      // device error word: a bounded wait in a kernel gave up (reported as HG_ERR_TIMEOUT)
     int mass_pending;  // mass / rho_bar below not yet read back from dsum
     double* staging;  // dense nz*ny*nx doubles, allocated on first host transfer
     double Q[hg::kMaxQ];
@@ -142,14 +148,19 @@ struct hg_grid {
     // carries lambda, and the running sum of lambda over the reverse sub-steps (float pair or double, padded layout)
     hg_grid* adj;
     void* acc[2];
-    // host I/O pipeline (hg_io_step): an upload and a download stream, two slots of device buffers and, per slot,
-    // events for "density uploaded", "density consumed", "acceleration written", "acceleration downloaded"
+    // host I/O pipeline (hg_io_step): an upload and a download stream, two slots of device buffers with, per slot,
+    // events for "density uploaded", "density consumed", "acceleration written", and a ring of completion events
+    // (one per call: its download has finished)
     cudaStream_t io_up, io_down;
     void* io_rho[2];
     void* io_acc[2];
     size_t io_rho_bytes, io_acc_bytes;
-    cudaEvent_t io_ev[2][4];
+    cudaEvent_t io_ev[2][3];
+    cudaEvent_t io_done[8];
     long long io_issued, io_waited;
+    // TMA tensor maps of the compensated-float state: hi[0..1], lo[0..1], dlt[0..1], s (stencil_tma.cu)
+    CUtensorMap tm[7];
+    int tm_ready;  // 0: not built, 1: built without dlt[1], 2: built with dlt[1]
 };
 
 namespace hg {
@@ -177,6 +188,9 @@ int adjoint_accumulate(hg_grid* a, void* acc_a, void* acc_b);
 int adjoint_gradient(hg_grid* a, const void* acc_a, const void* acc_b, void* out, int odt, double* scratch);
 int launch_periodic_fill(hg_grid* g, int b);         // periodic ghosts of time-level buffer b
 int launch_temporal(hg_grid* g, int k);              // k fused sub-steps: cur -> 1-cur (temporal.cu)
+struct SweepArgs;
+int launch_sweep_f32k_tma(hg_grid* g, const SweepArgs& A);  // TMA-staged compensated-float sweep (stencil_tma.cu)
+int device_error(hg_grid* g);                        // HG_ERR_TIMEOUT if a kernel's bounded wait gave up (syncs)
 int ensure_staging(hg_grid* g);
 int prepare_source(hg_grid* g, const void* src, int dtype);  // dense rho -> stored s, sum(rho) -> dsum (no sync)
 int sync_mass(hg_grid* g);                           // dsum -> host mass / rho_bar (syncs once per density)
@@ -199,7 +213,7 @@ int prof_fold(hg_grid* g);   // synchronise and add the recorded pairs to prof_m
 struct Bnd {
     int faces;              // 1: Robin ghosts to update (block epilogue)
     int periodic;           // 1: copy the new boundary cells into the opposite ghosts (block epilogue)
-    int xfaces;             // 0, or HG_BC_ROBIN / HG_BC_PERIODIC: the x-face ghosts are produced inside the sweep loop
+    int xfaces;             // 0, or HG_BC_PERIODIC: the x-face ghost copies are made inside the sweep loop
     const float2* robin32;  // (alpha, beta) per face ghost, compensated float grids
     const double* robin;    // (a = nu/mu, r_g, r_i) per face ghost, FP64 grids
     long long off[7];       // face offsets in the ghost enumeration (hg::Faces)

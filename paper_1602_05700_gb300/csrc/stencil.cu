@@ -5,10 +5,10 @@
 // over the interior of the padded layout (ghosts are filled by boundary.cu).  One kernel per precision:
 //
 // * f32k: float storage with compensated increments.  State per cell: hi + lo = phi^n (a float and its
-//   rounding remainder) and dlt = phi^n - phi^{n-1}.  The sub-step is
+//   rounding remainder, stored as a 16-bit code, cell.cuh) and dlt = phi^n - phi^{n-1}.  The sub-step is
 //       dlt' = dlt + (nu^2 (L(hi) + L(lo)) - s),   (hi', lo') = hi + (lo + dlt')  by Fast2Sum,
-//   so phi keeps ~48 bits while every array is float: 28 bytes of HBM traffic per cell (read hi, lo, dlt, rho;
-//   write hi', lo', dlt').  hi/lo ping-pong between two buffers (neighbours are read), dlt is updated in place.
+//   so phi keeps ~36 bits: 24 bytes of HBM traffic per cell (read hi 4, lo 2, dlt 4, s 4; write hi' 4, lo' 2,
+//   dlt' 4).  hi/lo ping-pong between two buffers (neighbours are read), dlt is updated in place.
 // * f64: double storage, phi^{n+1} written over phi^{n-1}: 32 bytes per cell.  GB300 issues few FP64
 //   instructions per clock (~0.5 T/s), and the update takes 15 of them (cell.cuh), so this kernel is bound by the
 //   FP64 pipe, not by HBM.
@@ -21,22 +21,21 @@
 // and z are masked (lanes beyond nx store nothing; the vector reads of the last group stay inside the padded row).
 #include "cell.cuh"
 #include "hg_internal.cuh"
+#include "sweep_f32k.cuh"
 
 namespace hg {
 
 namespace {
 
 __device__ __forceinline__ float4 ld4(const float* p) { return __ldg(reinterpret_cast<const float4*>(p)); }
+__device__ __forceinline__ uint2 ldl4(const lo_t* p) { return __ldg(reinterpret_cast<const uint2*>(p)); }
+__device__ __forceinline__ void stl4(lo_t* p, uint2 v) { *reinterpret_cast<uint2*>(p) = v; }
 __device__ __forceinline__ float4 ld4rw(const float* p) { return *reinterpret_cast<const float4*>(p); }
 __device__ __forceinline__ void st4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
 __device__ __forceinline__ double2 ld2(const double* p) { return __ldg(reinterpret_cast<const double2*>(p)); }
 __device__ __forceinline__ double2 ld2rw(const double* p) { return *reinterpret_cast<const double2*>(p); }
 __device__ __forceinline__ void st2(double* p, double2 v) { *reinterpret_cast<double2*>(p) = v; }
 
-__device__ __forceinline__ float el(const float4& v, int e) { return e == 0 ? v.x : e == 1 ? v.y : e == 2 ? v.z : v.w; }
-__device__ __forceinline__ void set(float4& v, int e, float x) {
-    if (e == 0) v.x = x; else if (e == 1) v.y = x; else if (e == 2) v.z = x; else v.w = x;
-}
 
 // Boundary work rides in the same launch, after each block's z-march (so it adds no registers to the sweep).  Robin:
 // a block next to a face updates the face ghosts that border its own cells -- its rows and planes of an x face, its
@@ -153,9 +152,9 @@ __device__ __forceinline__ void block_periodic_copies(const Layout& L, int x0, i
 template <int WY>
 __device__ __forceinline__ void sweep_f32k(const SweepArgs& A, int bx, int by, int bz) {
     const float* __restrict__ hi_c = (const float*)A.hi_c;
-    const float* __restrict__ lo_c = (const float*)A.lo_c;
+    const lo_t* __restrict__ lo_c = (const lo_t*)A.lo_c;
     float* __restrict__ hi_n = (float*)A.hi_n;
-    float* __restrict__ lo_n = (float*)A.lo_n;
+    lo_t* __restrict__ lo_n = (lo_t*)A.lo_n;
     float* __restrict__ dlt = (float*)A.dlt;
     const float* __restrict__ rho = (const float*)A.rho;
     const Layout& L = A.L;
@@ -167,7 +166,6 @@ __device__ __forceinline__ void sweep_f32k(const SweepArgs& A, int bx, int by, i
     const int i0 = bx * 128 + lane * 4;
     const bool active = i0 < L.nx;  // this lane owns cells
     const bool halo = i0 <= L.nx;   // this lane's group holds cells or the +x ghost (read for its left neighbour)
-    const bool full = i0 + 3 < L.nx;
     const int k0 = bz * zb;
     const int k1 = min(L.nz, k0 + zb);
     const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -176,31 +174,31 @@ __device__ __forceinline__ void sweep_f32k(const SweepArgs& A, int bx, int by, i
     float4 hm = z4, hc = z4, lm = z4, lc = z4;
     if (halo) {
         hm = ld4(hi_c + q - L.plane);
-        lm = ld4(lo_c + q - L.plane);
+        lm = lo_decode4(hm, ldl4(lo_c + q - L.plane));
         hc = ld4(hi_c + q);
-        lc = ld4(lo_c + q);
+        lc = lo_decode4(hc, ldl4(lo_c + q));
     }
     for (int k = k0; k < k1; ++k, q += L.plane) {
         float4 hp = z4, lp = z4, hs = z4, hn = z4, ls = z4, ln = z4, d = z4, r = z4;
         float hl = 0.f, hr = 0.f, ll = 0.f, lr = 0.f;
         if (halo) {
             hp = ld4(hi_c + q + L.plane);
-            lp = ld4(lo_c + q + L.plane);
+            lp = lo_decode4(hp, ldl4(lo_c + q + L.plane));
         }
         if (active) {
             hs = ld4(hi_c + q - L.pitch);
             hn = ld4(hi_c + q + L.pitch);
-            ls = ld4(lo_c + q - L.pitch);
-            ln = ld4(lo_c + q + L.pitch);
+            ls = lo_decode4(hs, ldl4(lo_c + q - L.pitch));
+            ln = lo_decode4(hn, ldl4(lo_c + q + L.pitch));
             d = ld4rw(dlt + q);
             r = ld4(rho + q);
             if (lane == 0) {
                 hl = __ldg(hi_c + q - 1);
-                ll = __ldg(lo_c + q - 1);
+                ll = lo_decode(hl, lo_c[q - 1]);
             }
             if (lane == 31 && i0 + 4 <= L.nx) {
                 hr = __ldg(hi_c + q + 4);
-                lr = __ldg(lo_c + q + 4);
+                lr = lo_decode(hr, lo_c[q + 4]);
             }
         }
         float shl = __shfl_up_sync(0xffffffffu, hc.w, 1), sll = __shfl_up_sync(0xffffffffu, lc.w, 1);
@@ -213,66 +211,9 @@ __device__ __forceinline__ void sweep_f32k(const SweepArgs& A, int bx, int by, i
             hr = shr;
             lr = slr;
         }
-        if (active) {
-            float4 ho, lo, dout;
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                float xl = e == 0 ? hl : el(hc, e - 1);
-                float xr = e == 3 ? hr : el(hc, e + 1);
-                float lxl = e == 0 ? ll : el(lc, e - 1);
-                float lxr = e == 3 ? lr : el(lc, e + 1);
-                float a, b, c;
-                f32k_update(xl, xr, el(hs, e), el(hn, e), el(hm, e), el(hp, e), el(hc, e), lxl, lxr, el(ls, e),
-                            el(ln, e), el(lm, e), el(lp, e), el(lc, e), el(d, e), el(r, e), nu2, a, b, c);
-                set(ho, e, a);
-                set(lo, e, b);
-                set(dout, e, c);
-            }
-            if (full) {
-                st4(hi_n + q, ho);
-                st4(lo_n + q, lo);
-                st4(dlt + q, dout);
-            } else {
-#pragma unroll
-                for (int e = 0; e < 4; ++e)
-                    if (i0 + e < L.nx) {
-                        hi_n[q + e] = el(ho, e);
-                        lo_n[q + e] = el(lo, e);
-                        dlt[q + e] = el(dout, e);
-                    }
-            }
-            // x-face ghosts of level n+1, by the two lanes that hold the face cells (the ghosts lie one element away
-            // in the same rows, so these stores are the only scattered ones, and they overlap the stream)
-            if (B.xfaces) {
-                const int elast = L.nx - 1 - i0;  // element holding cell nx-1, if 0..3
-                if (B.xfaces == HG_BC_ROBIN) {
-                    if (i0 == 0) {
-                        const float2 ab = B.robin32[B.off[0] + (long long)k * L.ny + j];
-                        float gh, gl;
-                        robin_update_f32k(ab.x, ab.y, hl, ll, hc.x, lc.x, gh, gl);
-                        hi_n[q - 1] = gh;
-                        lo_n[q - 1] = gl;
-                    }
-                    if (elast >= 0 && elast < 4) {
-                        const float2 ab = B.robin32[B.off[1] + (long long)k * L.ny + j];
-                        const float xg = elast == 3 ? hr : el(hc, elast + 1), lg = elast == 3 ? lr : el(lc, elast + 1);
-                        float gh, gl;
-                        robin_update_f32k(ab.x, ab.y, xg, lg, el(hc, elast), el(lc, elast), gh, gl);
-                        hi_n[q + elast + 1] = gh;
-                        lo_n[q + elast + 1] = gl;
-                    }
-                } else {  // periodic: cell 0 -> ghost nx, cell nx-1 -> ghost -1
-                    if (i0 == 0) {
-                        hi_n[q + L.nx] = ho.x;
-                        lo_n[q + L.nx] = lo.x;
-                    }
-                    if (elast >= 0 && elast < 4) {
-                        hi_n[q + elast - L.nx] = el(ho, elast);
-                        lo_n[q + elast - L.nx] = el(lo, elast);
-                    }
-                }
-            }
-        }
+        if (active)
+            group_update_store(L, B, nu2, i0, q, hc, lc, hl, ll, hr, lr, hs, hn, ls, ln, hm, hp, lm, lp, d, r,
+                               hi_n, lo_n, dlt);
         hm = hc;
         hc = hp;
         lm = lc;
@@ -288,9 +229,9 @@ __device__ __forceinline__ void sweep_f32k(const SweepArgs& A, int bx, int by, i
                 if (u < gb.n) {
                     ab[u] = B.robin32[gb.t[u]];
                     hg[u] = __ldg(hi_c + gb.qg[u]);
-                    lg[u] = __ldg(lo_c + gb.qg[u]);
+                    lg[u] = lo_decode(hg[u], lo_c[gb.qg[u]]);
                     hin[u] = __ldg(hi_c + gb.qi[u]);
-                    lin[u] = __ldg(lo_c + gb.qi[u]);
+                    lin[u] = lo_decode(hin[u], lo_c[gb.qi[u]]);
                 }
 #pragma unroll
             for (int u = 0; u < kGB; ++u)
@@ -298,7 +239,7 @@ __device__ __forceinline__ void sweep_f32k(const SweepArgs& A, int bx, int by, i
                     float gh, gl;
                     robin_update_f32k(ab[u].x, ab[u].y, hg[u], lg[u], hin[u], lin[u], gh, gl);
                     hi_n[gb.qg[u]] = gh;
-                    lo_n[gb.qg[u]] = gl;
+                    lo_n[gb.qg[u]] = lo_encode(gh, gl);
                 }
         });
     if (B.periodic) {
@@ -457,12 +398,13 @@ __global__ void __launch_bounds__(256) k_ghosts_robin(const SweepArgs A, int t0)
     ghost_cells(A.L, A.B, t, qg, qi, qo);
     if (A.prec == HG_PREC_F32K) {
         const float* hc = (const float*)A.hi_c;
-        const float* lc = (const float*)A.lo_c;
+        const lo_t* lc = (const lo_t*)A.lo_c;
         const float2 ab = A.B.robin32[t];
+        const float hg = __ldg(hc + qg), hi = __ldg(hc + qi);
         float gh, gl;
-        robin_update_f32k(ab.x, ab.y, __ldg(hc + qg), __ldg(lc + qg), __ldg(hc + qi), __ldg(lc + qi), gh, gl);
+        robin_update_f32k(ab.x, ab.y, hg, lo_decode(hg, lc[qg]), hi, lo_decode(hi, lc[qi]), gh, gl);
         ((float*)A.hi_n)[qg] = gh;
-        ((float*)A.lo_n)[qg] = gl;
+        ((lo_t*)A.lo_n)[qg] = lo_encode(gh, gl);
     } else {
         const double* pc = (const double*)A.hi_c;
         const double* R = A.B.robin;
@@ -478,13 +420,16 @@ __global__ void __launch_bounds__(256) k_ghosts_periodic(const SweepArgs A, int 
     ghost_cells(A.L, A.B, t, qg, qi, qo);
     if (A.prec == HG_PREC_F32K) {
         ((float*)A.hi_n)[qg] = ((const float*)A.hi_n)[qo];
-        ((float*)A.lo_n)[qg] = ((const float*)A.lo_n)[qo];
+        ((lo_t*)A.lo_n)[qg] = ((const lo_t*)A.lo_n)[qo];
     } else {
         ((double*)A.hi_n)[qg] = ((const double*)A.hi_n)[qo];
     }
 }
 
 int zchunk(const hg_grid* g) {
+    // compensated-float grids (TMA-staged sweep): short chunks, many blocks -- the stage ring hides the z warm-up,
+    // and fine blocks balance the SMs (measured at 512^3: 8 planes beat 16-64)
+    if (g->prec == HG_PREC_F32K) return g->nz < 8 ? g->nz : 8;
     // enough blocks for several waves on 152 SMs without making the z warm-up (2 planes) a large fraction; Robin
     // grids want about twice as many blocks (the blocks at the x faces also update the face ghosts, and finer
     // blocks balance that extra work better: measured 0.630 against 0.651 ms per sub-step at 512^3)
@@ -496,11 +441,6 @@ int zchunk(const hg_grid* g) {
     if (zb < 8) zb = 8;
     if (zb > g->nz) zb = g->nz;
     return zb;
-}
-
-template <int WY>
-__global__ void __launch_bounds__(32 * WY, 3) k_step_f32k(const SweepArgs A) {
-    sweep_f32k<WY>(A, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
 template <int WY>
@@ -562,33 +502,37 @@ SweepArgs sweep_args(const hg_grid* g, int zb) {
 
 unsigned sweep_blocks(const SweepArgs& A) { return A.gx * A.gy * (unsigned)((A.L.nz + A.zb - 1) / A.zb); }
 
-// A single grid's sub-step: [Robin ghost kernel] -> sweep -> [periodic ghost kernel].  The boundary work runs as
-// its own small launches here (measured cheaper than the sweep epilogue, which lengthens the boundary blocks); the
-// batched launch keeps the epilogue form.
+// A single grid's sub-step: [Robin ghost kernel] -> sweep -> [periodic ghost kernel].
+// Compensated-float grids: the TMA-staged sweep writes all Robin ghosts of level n+1 (x/y faces by its producer
+// warp from the staged level-n values, z faces by the first and last chunk) and copies the periodic x-face ghosts;
+// the periodic kernel covers the y and z faces with coalesced accesses.  FP64 grids: all ghosts in the small
+// kernels.
 int launch_step_single(hg_grid* g) {
     SweepArgs A = sweep_args(g, g->zb);
     const int robin = A.B.faces, periodic = A.B.periodic;
+    const bool f32k = g->prec == HG_PREC_F32K;
     A.B.faces = 0;
     A.B.periodic = 0;
-    if (g->prec == HG_PREC_F32K && (robin || periodic)) A.B.xfaces = g->bc;
-    const int t0 = A.B.xfaces ? (int)A.B.off[2] : 0;  // ghosts left to the separate kernels
-    dim3 block(32, kWY);
-    dim3 grid(A.gx, A.gy, (g->nz + A.zb - 1) / A.zb);
-    const unsigned gblocks = (unsigned)((A.B.off[6] - t0 + 255) / 256);
-    if (robin) {
-        k_ghosts_robin<<<gblocks, 256, 0, g->stream>>>(A, t0);
+    if (f32k && periodic) A.B.xfaces = HG_BC_PERIODIC;
+    const int t0r = f32k ? (int)A.B.off[6] : 0;  // first ghost left to the Robin kernel (none for f32k)
+    const int t0p = f32k ? (int)A.B.off[2] : 0;  // first ghost left to the periodic kernel
+    if (robin && t0r < A.B.off[6]) {
+        k_ghosts_robin<<<(unsigned)((A.B.off[6] - t0r + 255) / 256), 256, 0, g->stream>>>(A, t0r);
         HG_LAUNCHED("Robin ghost kernel");
     }
     int rc = prof_begin(g);
     if (rc) return rc;
-    if (g->prec == HG_PREC_F32K)
-        k_step_f32k<kWY><<<grid, block, 0, g->stream>>>(A);
-    else
-        k_step_f64<kWY><<<grid, block, 0, g->stream>>>(A);
-    HG_LAUNCHED("stencil sub-step kernel");
+    if (f32k) {
+        SweepArgs At = A;
+        At.B.faces = robin;  // x/y-face Robin ghosts by the producer warp
+        if ((rc = launch_sweep_f32k_tma(g, At))) return rc;
+    } else {
+        k_step_f64<kWY><<<dim3(A.gx, A.gy, (g->nz + A.zb - 1) / A.zb), dim3(32, kWY), 0, g->stream>>>(A);
+        HG_LAUNCHED("stencil sub-step kernel");
+    }
     if ((rc = prof_end(g))) return rc;
     if (periodic) {
-        k_ghosts_periodic<<<gblocks, 256, 0, g->stream>>>(A, t0);
+        k_ghosts_periodic<<<(unsigned)((A.B.off[6] - t0p + 255) / 256), 256, 0, g->stream>>>(A, t0p);
         HG_LAUNCHED("periodic ghost kernel");
     }
     return HG_OK;

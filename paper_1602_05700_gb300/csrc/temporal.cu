@@ -1,6 +1,8 @@
 // Temporal blocking: K consecutive sub-steps of the hyperbolic gravity equation per round trip through HBM
 // (arXiv 1602.05700, Sec. 2: rho is frozen during the wave sub-steps of a hydro step, so K sub-steps can be fused
-// without reading the source again).  FP32-compensated state only (hi + lo = phi^n, dlt = phi^n - phi^{n-1}).
+// without reading the source again).  FP32-compensated state only (hi + lo = phi^n with lo stored as a 16-bit
+// code, dlt = phi^n - phi^{n-1}).  The levels computed in registers round lo through its code exactly as a store
+// and a load would (lo_round), so nothing depends on whether a level passed through memory.
 //
 // A block of 32 x 32 threads owns a 32 x 32 column region of the x-y plane and marches in z through a chunk of
 // output planes.  Level 0 (the state at sub-step n) is read once per plane; level t = 1..K is computed one plane
@@ -17,8 +19,8 @@
 // and z in [-1, nz], so the face ghosts of level n+K (Robin updates, periodic copies) are written too.  Every update uses the arithmetic of cell.cuh,
 // so K fused sub-steps give bit-for-bit the result of K single sweeps.
 //
-// HBM bytes per cell per K sub-steps: read hi, lo, dlt, rho + write hi, lo, dlt = 28 B (plus halo re-reads, which
-// the neighbouring blocks mostly find in L2), i.e. 28/K B per cell-update against 28 B for a single sweep.
+// HBM bytes per cell per K sub-steps: read hi, lo, dlt, rho + write hi, lo, dlt = 24 B (plus halo re-reads, which
+// the neighbouring blocks mostly find in L2), i.e. 24/K B per cell-update against 24 B for a single sweep.
 #include "cell.cuh"
 #include "hg_internal.cuh"
 
@@ -30,11 +32,11 @@ constexpr int TB = 32;  // region side (threads per side)
 
 struct TParams {
     const float* hi_c;
-    const float* lo_c;
+    const lo_t* lo_c;
     const float* d_c;
     const float* rho;  // scaled source s
     float* hi_n;
-    float* lo_n;
+    lo_t* lo_n;
     float* d_n;
     const float2* robin32;  // (alpha, beta) per face ghost rounded to float, Robin only
     Layout L;
@@ -86,7 +88,7 @@ __device__ __forceinline__ void region_sweep(const TParams& P, float2 (*sh)[TB +
                          y <= L.ny;
     const long long col = loadable ? L.at(xw, yw, 0) : 0;
     const float* hi_c = P.hi_c + col;
-    const float* lo_c = P.lo_c + col;
+    const lo_t* lo_c = P.lo_c + col;
     const float* d_c = P.d_c + col;
     const float* rs = P.rho + col;
 
@@ -108,7 +110,7 @@ __device__ __forceinline__ void region_sweep(const TParams& P, float2 (*sh)[TB +
         }
         const long long o = (long long)(periodic ? pw : p) * L.plane;
         h = __ldg(hi_c + o);
-        l = __ldg(lo_c + o);
+        l = lo_decode(h, lo_c[o]);
         d = __ldg(d_c + o);
         r = __ldg(rs + o);
     };
@@ -148,6 +150,7 @@ __device__ __forceinline__ void region_sweep(const TParams& P, float2 (*sh)[TB +
                 const float2 ys = sh[b][ty][tx + 1], yn = sh[b][ty + 2][tx + 1];
                 f32k_update(xl.x, xr.x, ys.x, yn.x, qh[t - 1][0], qh[t - 1][2], c, xl.y, xr.y, ys.y, yn.y,
                             ql[t - 1][0], ql[t - 1][2], lc, dprev, rq[t], P.nu2, oh, ol, od);
+                if (t < K) ol = lo_round(oh, ol);
             } else if (robin && ((col_int && zg) || (EDGE && (col_fx || col_fy) && zin))) {
                 float2 in;
                 long long row;
@@ -163,6 +166,7 @@ __device__ __forceinline__ void region_sweep(const TParams& P, float2 (*sh)[TB +
                 }
                 const float2 ab = P.robin32[row];
                 robin_update_f32k(ab.x, ab.y, c, lc, in.x, in.y, oh, ol);
+                if (t < K) ol = lo_round(oh, ol);
             }
             if (t < K) {
                 qh[t][0] = qh[t][1];
@@ -181,16 +185,16 @@ __device__ __forceinline__ void region_sweep(const TParams& P, float2 (*sh)[TB +
                     const int nout = (x < 0 || x >= L.nx) + (y < 0 || y >= L.ny) + (pt < 0 || pt >= L.nz);
                     if (nout <= 1 && pt >= -1 && pt <= L.nz) {
                         P.hi_n[q] = oh;
-                        P.lo_n[q] = ol;
+                        P.lo_n[q] = lo_encode(oh, ol);
                         if (nout == 0) P.d_n[q] = od;
                     }
                 } else if (col_int && zin) {
                     P.hi_n[q] = oh;
-                    P.lo_n[q] = ol;
+                    P.lo_n[q] = lo_encode(oh, ol);
                     P.d_n[q] = od;
                 } else if (robin && ((col_int && zg) || (EDGE && (col_fx || col_fy) && zin))) {
                     P.hi_n[q] = oh;
-                    P.lo_n[q] = ol;
+                    P.lo_n[q] = lo_encode(oh, ol);
                 }
             }
         }
@@ -227,11 +231,11 @@ int launch_temporal(hg_grid* g, int k) {
     int nxt = 1 - g->cur;
     TParams P;
     P.hi_c = (const float*)g->phi[g->cur];
-    P.lo_c = (const float*)g->lo[g->cur];
+    P.lo_c = (const lo_t*)g->lo[g->cur];
     P.d_c = (const float*)g->dlt[g->dcur];
     P.rho = (const float*)g->rho;
     P.hi_n = (float*)g->phi[nxt];
-    P.lo_n = (float*)g->lo[nxt];
+    P.lo_n = (lo_t*)g->lo[nxt];
     P.d_n = (float*)g->dlt[1 - g->dcur];
     P.robin32 = g->robin32;
     P.L = g->L;

@@ -30,7 +30,15 @@ REPORT_METRICS = [
     ("launch__occupancy_limit_registers", "blocks/SM (register limit)"),
     ("launch__grid_size", "grid"),
     ("launch__block_size", "block"),
+    ("sm__inst_executed_pipe_lsu.avg.pct_of_peak_sustained_active", "LSU issue %"),
+    ("sm__inst_executed_pipe_xu.avg.pct_of_peak_sustained_active", "XU issue %"),
+    ("sm__inst_executed_pipe_adu.avg.pct_of_peak_sustained_active", "ADU issue %"),
     ("smsp__average_warps_issue_stalled_long_scoreboard_per_issue_active.ratio", "stall long scoreboard"),
+    ("smsp__average_warps_issue_stalled_short_scoreboard_per_issue_active.ratio", "stall short scoreboard"),
+    ("smsp__average_warps_issue_stalled_wait_per_issue_active.ratio", "stall wait"),
+    ("smsp__average_warps_issue_stalled_lg_throttle_per_issue_active.ratio", "stall LG throttle"),
+    ("smsp__average_warps_issue_stalled_mio_throttle_per_issue_active.ratio", "stall MIO throttle"),
+    ("smsp__average_warps_issue_stalled_not_selected_per_issue_active.ratio", "stall not selected"),
     ("smsp__average_warps_issue_stalled_barrier_per_issue_active.ratio", "stall barrier"),
     ("smsp__average_warps_issue_stalled_math_pipe_throttle_per_issue_active.ratio", "stall math pipe"),
     ("smsp__inst_executed.sum", "warp instructions"),

@@ -23,30 +23,33 @@ def densities(n, k, seed, dtype):
     return [I.blob_density(n, I.draw_blobs(2 + s % 3, seed + s)).astype(dtype) for s in range(k)]
 
 
+@pytest.mark.parametrize("keep", [1, 2])
 @pytest.mark.parametrize("n,prec,bc,dt", CASES)
-def test_io_step_equals_synchronous_calls(n, prec, bc, dt):
+def test_io_step_equals_synchronous_calls(n, prec, bc, dt, keep):
     lmax = 3 if bc == "multipole" else 0
     a = hg.Grid.unit_cube(n, precision=prec, bc=bc, lmax=lmax)
     b = hg.Grid.unit_cube(n, precision=prec, bc=bc, lmax=lmax)
-    rhos = densities(n, 5, 300 + n, dt)
+    rhos = densities(n, 6, 300 + n, dt)
     adt = np.float64 if prec == "f64" else np.float32
-    outs = [[np.empty((n, n, n), adt) for _ in range(3)] for _ in range(2)]
+    sets = keep + 1  # output buffer sets in rotation: `keep` calls in flight plus the one checked
+    outs = [[np.empty((n, n, n), adt) for _ in range(3)] for _ in range(sets)]
     want = []
     for s, rho in enumerate(rhos):
-        a.io_step(rho, 7, outs[s % 2])
-        a.io_wait(1)
-        if s > 0:  # the previous step is complete: check its output now, before its buffers are reused
-            for x, y in zip(outs[(s - 1) % 2], want[s - 1]):
-                assert np.array_equal(x, y), f"step {s - 1}"
+        a.io_step(rho, 7, outs[s % sets])
+        a.io_wait(keep)
+        if s >= keep:  # step s - keep is complete: check its output now, before its buffers are reused
+            for x, y in zip(outs[(s - keep) % sets], want[s - keep]):
+                assert np.array_equal(x, y), f"step {s - keep}"
         b.set_density(torch.from_numpy(rho).cuda())
         b.step(7)
         want.append([t.cpu().numpy() for t in b.accel(dtype=torch.float64 if prec == "f64" else torch.float32)])
     a.io_wait(0)
-    for x, y in zip(outs[(len(rhos) - 1) % 2], want[-1]):
-        assert np.array_equal(x, y)
+    for s in range(len(rhos) - keep, len(rhos)):
+        for x, y in zip(outs[s % sets], want[s]):
+            assert np.array_equal(x, y)
     assert np.array_equal(a.phi_ghosted(), b.phi_ghosted())
     sa, sb = a.stats(), b.stats()
-    assert sa["step"] == sb["step"] == 35
+    assert sa["step"] == sb["step"] == 7 * len(rhos)
     assert sa["mass"] == sb["mass"]
 
 
