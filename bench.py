@@ -56,26 +56,25 @@ def peaks():
     return FALLBACK_HBM_GBS, "fallback"
 
 
-def source_hash():
-    """sha256 over the CUDA sources, to tell whether a committed ncu figure was taken on the current kernels."""
+def source_hash(files=None):
+    """sha256 over CUDA sources (all of csrc/, or the given file names), to tell whether a committed ncu figure was
+    taken on the current kernels."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1602_05700_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
+    for f in sorted(files or os.listdir(csrc)):
         if f.endswith((".cu", ".cuh")):
             h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()
 
 
 def stencil_traffic(kernel, n):
-    """DRAM bytes per launch (scaled to n^3 cells) from profiles/traffic.json, if taken on the current sources."""
+    """DRAM bytes per launch (scaled to n^3 cells) from profiles/traffic.json, if taken on the current sources of
+    that kernel (the entry lists the files it is built from and their sha256)."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
-    d = json.load(open(p))
-    if d.get("csrc_sha256") != source_hash():
-        return None
-    e = d.get("kernels", {}).get(kernel)
-    if not e:
+    e = json.load(open(p)).get("kernels", {}).get(kernel)
+    if not e or e.get("sources_sha256") != source_hash(e.get("sources")):
         return None
     return round(e["dram_bytes_per_launch"] * (n ** 3) / e["cells"])
 
@@ -266,7 +265,9 @@ def run_ours(args, rank, world, local_rank):
     # host memory, with the copies of one step overlapping the sub-steps of the next (hg_io_step / hg_io_wait)
     if not args.skip_e2e:
         ke, we = max(4, min(steps, 10)), 2
-        host_rho = [rhos[s % len(rhos)].cpu().pin_memory() for s in range(we + ke)]
+        # a rotation of three page-locked host buffers for the density and three sets for -grad phi, as a hydro code
+        # with two steps in flight would keep them (each buffer is rewritten only after hg_io_wait has released it)
+        host_rho = [rhos[s].cpu().pin_memory() for s in range(3)]
         host_acc = [[torch.empty((n, n, n), dtype=torch.float32).pin_memory() for _ in range(3)] for _ in range(3)]
         g = hg.Grid(n, n, n, W["h"], W["origin"], W["c"], W["G"], W["dt"], "f32k", "robin")
         if best > 1:
@@ -274,7 +275,7 @@ def run_ours(args, rank, world, local_rank):
 
         def e2e_steps(first, count):
             for s in range(first, first + count):
-                g.io_step(host_rho[s], N_SUB, host_acc[s % 3])
+                g.io_step(host_rho[s % 3], N_SUB, host_acc[s % 3])
                 g.io_wait(2)  # step s-2 is done: its outputs are on the host, its buffers free again
             g.io_wait(0)
 

@@ -1,16 +1,19 @@
 // Many independent grids advanced together (the batching workload: uneven sizes, mixed precisions).
 //
 // One sub-step of every grid is one batched kernel launch (stencil.cu, k_step_batch: block -> grid by a prefix
-// table, FP32-compensated and FP64 grids in the same launch; boundary ghosts are written in the sweep's epilogue).  hg_batch_step(b, n) records the n sub-steps once as a CUDA graph on the batch's own stream
-// and replays it with a single graph launch; the kernels read the per-grid arguments from two device tables (for
-// the two time-level parities), refreshed from the grids before every replay, so the graph stays valid while the
-// grids' states move on.  Results are identical to stepping each grid on its own: the per-cell arithmetic is the
-// same code.
+// table; compensated-float grids run the TMA-staged sweep with their tensor maps in the table, FP64 grids the
+// register-staged FP64 sweep, in the same launch, so HBM-bound and FP64-bound blocks share the SMs; boundary ghosts
+// are written inside the launch).  hg_batch_step(b, n) records the n sub-steps once as a CUDA graph on the batch's
+// own stream and replays it with a single graph launch; the kernels read the per-grid arguments from two device
+// tables (for the two time-level parities), refreshed from the grids before every replay, so the graph stays valid
+// while the grids' states move on.  Results are identical to stepping each grid on its own: the per-cell arithmetic
+// is the same code.
 //
-// Autotuning: the z extent of a block (planes per block, which sets the number of blocks and the share of the
-// z warm-up) is chosen from a few candidates by timing the first sub-steps of the first hg_batch_step with CUDA
-// events -- every candidate computes the same result, so the timing runs are real sub-steps -- and cached per
-// (device, set of grid shapes/precisions/boundaries) for the process.
+// Autotuning: the z extent of an FP64 block (planes per block, which sets the number of blocks and the share of
+// the z warm-up) is chosen from a few candidates by timing the first sub-steps of the first hg_batch_step with
+// CUDA events -- every candidate computes the same result, so the timing runs are real sub-steps -- and cached per
+// (device, set of grid shapes/precisions/boundaries) for the process.  The TMA-staged blocks of the compensated-float
+// grids use 8 planes, where their stage ring hides the z warm-up.
 #include <stdio.h>
 #include <string.h>
 
@@ -30,7 +33,7 @@ struct hg_batch {
     int device;
     cudaStream_t stream;  // own non-blocking stream (graphs cannot be captured on the legacy default stream)
     cudaEvent_t ev_in, ev_out;
-    SweepArgs* d_tab[2];
+    TmaEntry* d_tab[2];   // per-grid entries, per parity
     unsigned* d_first;
     unsigned total_blocks;
     std::vector<unsigned> first;
@@ -63,20 +66,30 @@ std::string tune_key(const hg_batch* b) {
 
 // device tables for the sub-step that starts from parity p (0: every grid's current level, 1: the next one)
 int upload_tables(hg_batch* b) {
-    std::vector<SweepArgs> tab[2];
+    std::vector<TmaEntry> tab[2];
     for (int p = 0; p < 2; ++p) {
         for (hg_grid* g : b->grids) {
             const int cur = g->cur;
             g->cur = cur ^ p;
-            tab[p].push_back(sweep_args(g, b->zb));
+            TmaEntry e;
+            memset(&e, 0, sizeof e);
+            int rc = HG_OK;
+            if (g->prec == HG_PREC_F32K) {
+                rc = tma_entry(g, &e);  // TMA-staged blocks: a fixed 8-plane chunk
+            } else {
+                e.A = sweep_args(g, b->zb);
+                e.err = g->derr;
+            }
             g->cur = cur;
+            if (rc) return rc;
+            tab[p].push_back(e);
         }
     }
     b->first.assign(1, 0);
-    for (const SweepArgs& a : tab[0]) b->first.push_back(b->first.back() + sweep_blocks(a));
+    for (const TmaEntry& e : tab[0]) b->first.push_back(b->first.back() + sweep_blocks(e.A));
     b->total_blocks = b->first.back();
     for (int p = 0; p < 2; ++p)
-        HG_CUDA(cudaMemcpyAsync(b->d_tab[p], tab[p].data(), tab[p].size() * sizeof(SweepArgs), cudaMemcpyHostToDevice,
+        HG_CUDA(cudaMemcpyAsync(b->d_tab[p], tab[p].data(), tab[p].size() * sizeof(TmaEntry), cudaMemcpyHostToDevice,
                                 b->stream));
     HG_CUDA(cudaMemcpyAsync(b->d_first, b->first.data(), b->first.size() * sizeof(unsigned), cudaMemcpyHostToDevice,
                             b->stream));
@@ -84,7 +97,7 @@ int upload_tables(hg_batch* b) {
     return HG_OK;
 }
 
-// the launches of one sub-step of parity p
+// the launch of one sub-step of parity p
 int enqueue_substep(hg_batch* b, int p) { return launch_step_batch(b->stream, b->d_tab[p], b->d_first, b->n, b->total_blocks); }
 
 void advance(hg_batch* b, int n) {
@@ -94,7 +107,7 @@ void advance(hg_batch* b, int n) {
     }
 }
 
-// pick the planes per block by timing one sub-step per candidate (real sub-steps: every candidate gives the same
+// pick the planes per block by timing two sub-steps per candidate (real sub-steps: every candidate gives the same
 // result); returns the number of sub-steps taken
 int autotune(hg_batch* b, int budget, int* taken) {
     *taken = 0;
@@ -107,6 +120,12 @@ int autotune(hg_batch* b, int budget, int* taken) {
             return upload_tables(b);
         }
     }
+    bool any64 = false;
+    for (hg_grid* g : b->grids) any64 = any64 || g->prec == HG_PREC_F64;
+    if (!any64) {  // nothing to tune: the TMA-staged blocks use a fixed chunk
+        b->zb = 8;
+        return upload_tables(b);
+    }
     const int cand[] = {8, 16, 32, 64};
     int best = 0;
     float best_ms = 0.f;
@@ -116,10 +135,12 @@ int autotune(hg_batch* b, int budget, int* taken) {
     int rc = HG_OK;
     for (int c : cand) {
         if (*taken >= budget) break;
+        if (*taken + 2 > budget) break;
         b->zb = c;
         if ((rc = upload_tables(b))) break;
         cudaEventRecord(e0, b->stream);
-        if ((rc = enqueue_substep(b, 0))) break;
+        if ((rc = enqueue_substep(b, 0))) break;  // two sub-steps (both parities) per candidate
+        if ((rc = enqueue_substep(b, 1))) break;
         cudaEventRecord(e1, b->stream);
         cudaError_t e = cudaEventSynchronize(e1);
         if (e != cudaSuccess) {
@@ -128,8 +149,8 @@ int autotune(hg_batch* b, int budget, int* taken) {
         }
         float ms = 0.f;
         cudaEventElapsedTime(&ms, e0, e1);
-        advance(b, 1);
-        ++*taken;
+        advance(b, 2);
+        *taken += 2;
         if (best == 0 || ms < best_ms) {
             best = c;
             best_ms = ms;
@@ -140,7 +161,7 @@ int autotune(hg_batch* b, int budget, int* taken) {
     if (rc) return rc;
     if (best == 0) return HG_OK;  // no budget to tune: keep the default rule this time
     b->zb = best;
-    if (*taken == (int)(sizeof cand / sizeof cand[0])) {
+    if (*taken == 2 * (int)(sizeof cand / sizeof cand[0])) {
         std::lock_guard<std::mutex> lock(g_tune_mu);
         g_tuned[key] = best;
     }
@@ -193,7 +214,7 @@ int hg_batch_create(hg_grid* const* grids, int n, hg_batch** out) {
     ck(cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking), "cudaStreamCreate");
     ck(cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming), "cudaEventCreate");
     ck(cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming), "cudaEventCreate");
-    for (int p = 0; p < 2 && rc == HG_OK; ++p) ck(cudaMalloc(&b->d_tab[p], n * sizeof(SweepArgs)), "cudaMalloc(table)");
+    for (int p = 0; p < 2 && rc == HG_OK; ++p) ck(cudaMalloc(&b->d_tab[p], n * sizeof(TmaEntry)), "cudaMalloc(table)");
     ck(cudaMalloc(&b->d_first, (n + 1) * sizeof(unsigned)), "cudaMalloc(table)");
     if (rc == HG_OK) rc = upload_tables(b);
     if (rc != HG_OK) {

@@ -161,6 +161,8 @@ struct hg_grid {
     // TMA tensor maps of the compensated-float state: hi[0..1], lo[0..1], dlt[0..1], s (stencil_tma.cu)
     CUtensorMap tm[7];
     int tm_ready;  // 0: not built, 1: built without dlt[1], 2: built with dlt[1]
+    CUtensorMap tm2[7];  // the same arrays with the boxes of the depth-2 kernel (temporal_tma.cu)
+    int tm2_ready;
 };
 
 namespace hg {
@@ -190,6 +192,7 @@ int launch_periodic_fill(hg_grid* g, int b);         // periodic ghosts of time-
 int launch_temporal(hg_grid* g, int k);              // k fused sub-steps: cur -> 1-cur (temporal.cu)
 struct SweepArgs;
 int launch_sweep_f32k_tma(hg_grid* g, const SweepArgs& A);  // TMA-staged compensated-float sweep (stencil_tma.cu)
+int launch_temporal2_tma(hg_grid* g);                // two fused TMA-staged sub-steps (temporal_tma.cu)
 int device_error(hg_grid* g);                        // HG_ERR_TIMEOUT if a kernel's bounded wait gave up (syncs)
 int ensure_staging(hg_grid* g);
 int prepare_source(hg_grid* g, const void* src, int dtype);  // dense rho -> stored s, sum(rho) -> dsum (no sync)
@@ -237,8 +240,19 @@ struct SweepArgs {
 };
 
 SweepArgs sweep_args(const hg_grid* g, int zb);  // sub-step cur -> 1 - cur of grid g; zb = 0: default z chunk
+// a 3-D TMA map over a padded array (pitch x (ny+2) x (nz+2) elements of `bytes` each), boxes box_x x box_y x 1
+int tma_encode(CUtensorMap* m, void* base, const Layout& L, int bytes, int box_x, int box_y);
+
+// One grid of a batched launch: its sweep arguments and, for a compensated-float grid, the tensor maps of its state
+// (hi, lo codes, dlt, s of level n) and its error word.
+struct alignas(128) TmaEntry {
+    CUtensorMap m[4];
+    SweepArgs A;
+    int* err;
+};
+int tma_entry(hg_grid* g, TmaEntry* e);  // compensated-float g's sub-step cur -> 1 - cur (all ghosts in the launch)
+int launch_step_batch(cudaStream_t st, const TmaEntry* tab, const unsigned* first, int n, unsigned total_blocks);
 unsigned sweep_blocks(const SweepArgs& A);
-int launch_step_batch(cudaStream_t st, const SweepArgs* tab, const unsigned* first, int n, unsigned total_blocks);
 
 // ---- deterministic reductions --------------------------------------------------------------------------------
 constexpr int kRedThreads = 256;

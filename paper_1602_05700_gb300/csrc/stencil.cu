@@ -22,6 +22,7 @@
 #include "cell.cuh"
 #include "hg_internal.cuh"
 #include "sweep_f32k.cuh"
+#include "sweep_tma.cuh"
 
 namespace hg {
 
@@ -108,47 +109,6 @@ __device__ __forceinline__ void block_face_ghosts(const Layout& L, const Bnd& B,
         }, upd);
 }
 
-// Periodic boundaries: after its own sweep (and a block barrier, so that the block sees what its threads wrote),
-// a block copies the new values of its cells on a face into the ghosts of the opposite face.  copy(src, dst) takes
-// padded indices; each boundary cell belongs to exactly one block.
-template <class Copy>
-__device__ __forceinline__ void block_periodic_copies(const Layout& L, int x0, int j0, int wy, int k0, int k1, int bx,
-                                                      int by, int gx, int gy, Copy&& copy) {
-    const int tid = threadIdx.y * blockDim.x + threadIdx.x, nth = blockDim.x * blockDim.y;
-    const int jn = min(wy, L.ny - j0), xn = min(128, L.nx - x0), kn = k1 - k0;
-    const long long wx = L.nx, wy_ = (long long)L.ny * L.pitch, wz = (long long)L.nz * L.plane;
-    if (bx == 0)
-        for (int t = tid; t < jn * kn; t += nth) {
-            const long long q = L.at(0, j0 + t % jn, k0 + t / jn);
-            copy(q, q + wx);
-        }
-    if (bx == gx - 1)
-        for (int t = tid; t < jn * kn; t += nth) {
-            const long long q = L.at(L.nx - 1, j0 + t % jn, k0 + t / jn);
-            copy(q, q - wx);
-        }
-    if (by == 0)
-        for (int t = tid; t < xn * kn; t += nth) {
-            const long long q = L.at(x0 + t % xn, 0, k0 + t / xn);
-            copy(q, q + wy_);
-        }
-    if (by == gy - 1)
-        for (int t = tid; t < xn * kn; t += nth) {
-            const long long q = L.at(x0 + t % xn, L.ny - 1, k0 + t / xn);
-            copy(q, q - wy_);
-        }
-    if (k0 == 0)
-        for (int t = tid; t < xn * jn; t += nth) {
-            const long long q = L.at(x0 + t % xn, j0 + t / xn, 0);
-            copy(q, q + wz);
-        }
-    if (k1 == L.nz)
-        for (int t = tid; t < xn * jn; t += nth) {
-            const long long q = L.at(x0 + t % xn, j0 + t / xn, L.nz - 1);
-            copy(q, q - wz);
-        }
-}
-
 template <int WY>
 __device__ __forceinline__ void sweep_f32k(const SweepArgs& A, int bx, int by, int bz) {
     const float* __restrict__ hi_c = (const float*)A.hi_c;
@@ -169,7 +129,7 @@ __device__ __forceinline__ void sweep_f32k(const SweepArgs& A, int bx, int by, i
     const int k0 = bz * zb;
     const int k1 = min(L.nz, k0 + zb);
     const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (j < L.ny) {  // whole warps: rows past ny only join the boundary epilogue
+    if (j < L.ny && (int)threadIdx.y < WY) {  // rows past ny (or extra warps) only join the epilogue
     long long q = L.at(i0, j, k0);
     float4 hm = z4, hc = z4, lm = z4, lc = z4;
     if (halo) {
@@ -244,7 +204,8 @@ __device__ __forceinline__ void sweep_f32k(const SweepArgs& A, int bx, int by, i
         });
     if (B.periodic) {
         __syncthreads();
-        block_periodic_copies(L, bx * 128, by * WY, WY, k0, k1, bx, by, A.gx, A.gy, [&](long long q, long long d) {
+        block_periodic_copies(L, bx * 128, by * WY, WY, k0, k1, bx, by, A.gx, A.gy, block_tid(), block_nth(),
+                              [&](long long q, long long d) {
             hi_n[d] = hi_n[q];
             lo_n[d] = lo_n[q];
         });
@@ -294,7 +255,7 @@ __device__ __forceinline__ void sweep_f64(const SweepArgs& A, int bx, int by, in
     D4 zero;
 #pragma unroll
     for (int e = 0; e < 4; ++e) zero.v[e] = 0.0;
-    if (j < L.ny) {  // whole warps: rows past ny only join the boundary epilogue
+    if (j < L.ny && (int)threadIdx.y < WY) {  // rows past ny (or extra warps) only join the epilogue
     long long q = L.at(i0, j, k0);
     D4 cm = zero, cc = zero;
     if (halo) {
@@ -356,7 +317,7 @@ __device__ __forceinline__ void sweep_f64(const SweepArgs& A, int bx, int by, in
         });
     if (B.periodic) {
         __syncthreads();
-        block_periodic_copies(L, bx * 128, by * WY, WY, k0, k1, bx, by, A.gx, A.gy,
+        block_periodic_copies(L, bx * 128, by * WY, WY, k0, k1, bx, by, A.gx, A.gy, block_tid(), block_nth(),
                               [&](long long q, long long d) { phi_pn[d] = phi_pn[q]; });
     }
 }
@@ -448,12 +409,16 @@ __global__ void __launch_bounds__(32 * WY, 2) k_step_f64(const SweepArgs A) {
     sweep_f64<WY>(A, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
-// One launch for the sub-step of many grids: block b belongs to the grid g with first[g] <= b < first[g+1]
-// (binary search in the prefix table), and runs that grid's sweep body for its local block coordinates.  Grids of
-// both precisions mix in one launch (the branch is uniform per block).
-template <int WY>
-__global__ void __launch_bounds__(32 * WY, 2) k_step_batch(const SweepArgs* __restrict__ tab,
-                                                           const unsigned* __restrict__ first, int n) {
+// One launch for the sub-step of many grids: block b belongs to the entry e with first[e] <= b < first[e+1]
+// (binary search in the prefix table).  Compensated-float entries run the TMA-staged sweep (their tensor maps live in
+// the table, in global memory; the issuing thread acquires them through the tensormap proxy before its first copy),
+// FP64 entries the register-staged FP64 sweep on the first kTmaWY warps, with the last warp joining only its
+// boundary epilogue.  Grids of both precisions share the launch, so FP64-bound and HBM-bound blocks run side by side.
+template <int WY, int S>
+__global__ void __launch_bounds__(32 * (WY + 1), 2) k_step_batch(const TmaEntry* __restrict__ tab,
+                                                                 const unsigned* __restrict__ first, int n) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ __align__(8) unsigned long long bars[2 * S];
     const unsigned b = blockIdx.x;
     int lo = 0, hi = n - 1;
     while (lo < hi) {
@@ -463,13 +428,17 @@ __global__ void __launch_bounds__(32 * WY, 2) k_step_batch(const SweepArgs* __re
         else
             hi = mid - 1;
     }
-    const SweepArgs& A = tab[lo];
+    const TmaEntry& E = tab[lo];
     const unsigned local = b - __ldg(first + lo);
-    const int bx = (int)(local % A.gx), by = (int)((local / A.gx) % A.gy), bz = (int)(local / (A.gx * A.gy));
-    if (A.prec == HG_PREC_F32K)
-        sweep_f32k<WY>(A, bx, by, bz);
-    else
-        sweep_f64<WY>(A, bx, by, bz);
+    const int bx = (int)(local % E.A.gx), by = (int)((local / E.A.gx) % E.A.gy), bz = (int)(local / (E.A.gx * E.A.gy));
+    if (E.A.prec == HG_PREC_F32K) {
+        if (threadIdx.y == WY && threadIdx.x == 0)  // the producer's issuing thread
+            for (int m = 0; m < 4; ++m)
+                asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&E.m[m]) : "memory");
+        tma_sweep<WY, S>(&E.m[0], &E.m[1], &E.m[2], &E.m[3], E.A, bx, by, bz, E.err, smem, bars);
+    } else {
+        sweep_f64<WY>(E.A, bx, by, bz);
+    }
 }
 
 }  // namespace
@@ -538,8 +507,15 @@ int launch_step_single(hg_grid* g) {
     return HG_OK;
 }
 
-int launch_step_batch(cudaStream_t st, const SweepArgs* tab, const unsigned* first, int n, unsigned total_blocks) {
-    k_step_batch<kWY><<<total_blocks, dim3(32, kWY), 0, st>>>(tab, first, n);
+int launch_step_batch(cudaStream_t st, const TmaEntry* tab, const unsigned* first, int n, unsigned total_blocks) {
+    static bool attr_set = false;
+    const int smem = kStages * StageGeom<kTmaWY>::bytes;
+    if (!attr_set) {
+        HG_CUDA(cudaFuncSetAttribute(k_step_batch<kTmaWY, kStages>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     smem));
+        attr_set = true;
+    }
+    k_step_batch<kTmaWY, kStages><<<total_blocks, dim3(32, kTmaWY + 1), smem, st>>>(tab, first, n);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "batched sub-step kernel");
     return HG_OK;

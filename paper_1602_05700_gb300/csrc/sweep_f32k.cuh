@@ -66,4 +66,47 @@ __device__ __forceinline__ void group_update_store(const Layout& L, const Bnd& B
     }
 }
 
+__device__ __forceinline__ int block_tid() { return threadIdx.y * blockDim.x + threadIdx.x; }
+__device__ __forceinline__ int block_nth() { return blockDim.x * blockDim.y; }
+
+// Periodic boundaries: after its own sweep (and a barrier among the threads that wrote it, so that they see each
+// other's stores), a block copies the new values of its cells on a face into the ghosts of the opposite face, with
+// threads tid = 0 .. nth-1.  copy(src, dst) takes padded indices; each boundary cell belongs to exactly one block.
+template <class Copy>
+__device__ __forceinline__ void block_periodic_copies(const Layout& L, int x0, int j0, int wy, int k0, int k1, int bx,
+                                                      int by, int gx, int gy, int tid, int nth, Copy&& copy) {
+    const int jn = min(wy, L.ny - j0), xn = min(128, L.nx - x0), kn = k1 - k0;
+    const long long wx = L.nx, wy_ = (long long)L.ny * L.pitch, wz = (long long)L.nz * L.plane;
+    if (bx == 0)
+        for (int t = tid; t < jn * kn; t += nth) {
+            const long long q = L.at(0, j0 + t % jn, k0 + t / jn);
+            copy(q, q + wx);
+        }
+    if (bx == gx - 1)
+        for (int t = tid; t < jn * kn; t += nth) {
+            const long long q = L.at(L.nx - 1, j0 + t % jn, k0 + t / jn);
+            copy(q, q - wx);
+        }
+    if (by == 0)
+        for (int t = tid; t < xn * kn; t += nth) {
+            const long long q = L.at(x0 + t % xn, 0, k0 + t / xn);
+            copy(q, q + wy_);
+        }
+    if (by == gy - 1)
+        for (int t = tid; t < xn * kn; t += nth) {
+            const long long q = L.at(x0 + t % xn, L.ny - 1, k0 + t / xn);
+            copy(q, q - wy_);
+        }
+    if (k0 == 0)
+        for (int t = tid; t < xn * jn; t += nth) {
+            const long long q = L.at(x0 + t % xn, j0 + t / xn, 0);
+            copy(q, q + wz);
+        }
+    if (k1 == L.nz)
+        for (int t = tid; t < xn * jn; t += nth) {
+            const long long q = L.at(x0 + t % xn, j0 + t / xn, L.nz - 1);
+            copy(q, q - wz);
+        }
+}
+
 }  // namespace hg

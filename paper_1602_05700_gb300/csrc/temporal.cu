@@ -228,6 +228,7 @@ int launch_k(hg_grid* g, const TParams& P, int zchunk) {
 
 int launch_temporal(hg_grid* g, int k) {
     if (g->prec != HG_PREC_F32K || !g->dlt[1]) return fail(HG_ERR_STATE, "temporal blocking needs an f32k grid");
+    if (k == 2 && g->bc != HG_BC_PERIODIC) return launch_temporal2_tma(g);  // the TMA-staged depth-2 kernel
     int nxt = 1 - g->cur;
     TParams P;
     P.hi_c = (const float*)g->phi[g->cur];
