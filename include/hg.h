@@ -20,7 +20,9 @@
  *
  * Conventions for every entry point:
  *   - Return value: HG_OK (0) or a negative HG_ERR_* code; hg_last_error() then gives a message (thread-local).
- *     No call aborts, traps or waits without bound.
+ *     No call aborts, traps or waits without bound: every wait inside a kernel has a time limit (1 s), after which
+ *     the kernel records the failure in the grid's device error word and returns; hg_sync and hg_get_stats then
+ *     report HG_ERR_TIMEOUT.
  *   - Array arguments are plain pointers.  Unless stated otherwise an array is nz*ny*nx elements in C order
  *     (z slowest, x fastest), no padding, of the element type given by a dtype argument (HG_DT_F32 = float,
  *     HG_DT_F64 = double).  A flag *_on_device says whether a pointer is device memory of the grid's device
@@ -210,6 +212,14 @@ int hg_io_step(hg_grid* g, const void* rho_host, int rho_dtype, int n_substeps, 
 /* Block until all but the newest `keep` hg_io_step calls have finished (their host buffers are then the caller's
  * again and the accelerations are in place).  keep = 0 waits for every call. */
 int hg_io_wait(hg_grid* g, int keep);
+
+/*
+ * Diagnostic of the bounded waits inside the kernels: launches a one-block kernel that waits (1 ms limit) on an
+ * mbarrier nothing will complete, then reads the grid's device error word as hg_sync does.  Returns HG_OK when the
+ * wait gave up and the timeout was reported (the error word is cleared again), HG_ERR_STATE when it was not, or the
+ * error of an earlier launch if one was pending.  Synchronises the stream.
+ */
+int hg_check_bounded_wait(hg_grid* g);
 
 /* Block until the grid's streams are idle; HG_ERR_CUDA carries any pending asynchronous error. */
 int hg_sync(hg_grid* g);

@@ -179,6 +179,10 @@ class Grid:
         _lib.check(_lib.lib().hg_io_step(self.handle, rp, rcode, int(n), *ptrs, acode))
         self._io_keep.append(keep)
 
+    def check_bounded_wait(self):
+        """Run the kernels' bounded-wait diagnostic (a wait that cannot complete must give up and be reported)."""
+        _lib.check(_lib.lib().hg_check_bounded_wait(self.handle))
+
     def io_wait(self, keep=0):
         """Block until all but the newest `keep` io_step calls are done (their outputs are then filled)."""
         _lib.check(_lib.lib().hg_io_wait(self.handle, int(keep)))

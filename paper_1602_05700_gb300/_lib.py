@@ -73,6 +73,7 @@ SIGNATURES = {
     "hg_profile_read": (_I, [_V, _P(_D), _P(ctypes.c_longlong), _P(ctypes.c_longlong)]),
     "hg_io_step": (_I, [_V, _V, _I, _I, _V, _V, _V, _I]),
     "hg_io_wait": (_I, [_V, _I]),
+    "hg_check_bounded_wait": (_I, [_V]),
     "hg_sync": (_I, [_V]),
     "hg_free": (None, [_V]),
     "hg_batch_create": (_I, [_P(_V), _I, _P(_V)]),

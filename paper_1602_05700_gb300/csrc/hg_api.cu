@@ -732,6 +732,16 @@ int hg_io_wait(hg_grid* g, int keep) {
     return HG_OK;
 }
 
+int hg_check_bounded_wait(hg_grid* g) {
+    int rc = check_grid(g);
+    if (rc) return rc;
+    if ((rc = device_error(g))) return rc;  // an earlier error is reported as such, not taken for the self-test's
+    rc = wait_selftest(g);
+    if (rc == HG_ERR_TIMEOUT) return HG_OK;  // the wait gave up and the host saw it
+    if (rc == HG_OK) return fail(HG_ERR_STATE, "the bounded-wait self-test did not report its timeout");
+    return rc;
+}
+
 int hg_sync(hg_grid* g) {
     int rc = check_grid(g);
     if (rc) return rc;

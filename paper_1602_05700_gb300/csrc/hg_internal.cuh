@@ -194,6 +194,7 @@ struct SweepArgs;
 int launch_sweep_f32k_tma(hg_grid* g, const SweepArgs& A);  // TMA-staged compensated-float sweep (stencil_tma.cu)
 int launch_temporal2_tma(hg_grid* g);                // two fused TMA-staged sub-steps (temporal_tma.cu)
 int device_error(hg_grid* g);                        // HG_ERR_TIMEOUT if a kernel's bounded wait gave up (syncs)
+int wait_selftest(hg_grid* g);                       // a wait that cannot complete, then device_error (stencil_tma.cu)
 int ensure_staging(hg_grid* g);
 int prepare_source(hg_grid* g, const void* src, int dtype);  // dense rho -> stored s, sum(rho) -> dsum (no sync)
 int sync_mass(hg_grid* g);                           // dsum -> host mass / rho_bar (syncs once per density)

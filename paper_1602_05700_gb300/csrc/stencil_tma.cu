@@ -20,6 +20,17 @@ __global__ void __launch_bounds__(32 * (WY + 1), 3)
     tma_sweep<WY, S>(&m_hi, &m_lo, &m_d, &m_s, A, blockIdx.x, blockIdx.y, blockIdx.z, err, smem, bars);
 }
 
+// the bounded-wait path itself: an mbarrier that nothing ever arrives on, waited for with a short limit
+__global__ void k_wait_selftest(int* err, unsigned long long limit_ns) {
+    __shared__ __align__(8) unsigned long long bar;
+    if (threadIdx.x == 0) {
+        mbar_init(smem_addr(&bar), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    mbar_wait(smem_addr(&bar), 0u, err, limit_ns);
+}
+
 using TmaEncode = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
@@ -111,6 +122,12 @@ int tma_entry(hg_grid* g, TmaEntry* e) {
     e->A.B.xfaces = 0;
     e->err = g->derr;
     return HG_OK;
+}
+
+int wait_selftest(hg_grid* g) {
+    k_wait_selftest<<<1, 32, 0, g->stream>>>(g->derr, 1000000ull);  // 1 ms
+    HG_LAUNCHED("bounded-wait self-test kernel");
+    return device_error(g);
 }
 
 }  // namespace hg

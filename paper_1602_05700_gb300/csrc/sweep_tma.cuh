@@ -74,11 +74,12 @@ __device__ __forceinline__ bool mbar_test(uint32_t bar, unsigned parity) {
     return ok != 0;
 }
 // wait for the phase of the given parity to complete; false (and the error word set) after kWaitNs
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, unsigned parity, int* err) {
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, unsigned parity, int* err,
+                                          unsigned long long limit_ns = kWaitNs) {
     if (mbar_test(bar, parity)) return true;
     const unsigned long long t0 = now_ns();
     while (!mbar_test(bar, parity)) {
-        if (now_ns() - t0 > kWaitNs) {
+        if (now_ns() - t0 > limit_ns) {
             atomicOr(err, 1);
             return false;
         }

@@ -4,12 +4,12 @@
 //
 // A block writes a tile of 120 x-cells x 8 rows of level n+2 over a chunk of z planes.  Level n+1 is computed on
 // the tile grown by one cell on every side (x0-4 .. x0+123, rows j0-1 .. j0+8: 32 lanes x 4 cells, one warp per
-// row, 10 consumer warps), from level n staged by a producer warp with cp.async.bulk.tensor into a ring of 4
-// shared-memory stages (per plane: hi and lo-code rows j0-2 .. j0+9 over cells x0-12 .. x0+131, dlt and s rows
+// row, 10 warps), from level n staged with cp.async.bulk.tensor into a ring of 3 shared-memory stages (per plane: hi and lo-code rows j0-2 .. j0+9 over cells x0-12 .. x0+131, dlt and s rows
 // j0-1 .. j0+8 over x0-4 .. x0+123).  In z the two levels form a pipeline: the iteration that computes level n+1 at
 // plane p (its own row's -z/centre planes in registers, +z and the y rows from the stage) writes that row into a
-// 3-slot shared ring, meets the other consumer warps at one named barrier, and then computes level n+2 at plane
-// p-1 from its own level-(n+1) rows in registers and the neighbouring rows in the ring.  Level n+1 is never stored.
+// 4-slot shared ring, meets the other warps at one named barrier -- after which one thread refills the stage of
+// plane p with plane p+3 -- and then computes level n+2 at plane p-1 from the ring (its own rows at planes p-2, p-1,
+// the neighbouring rows at p-1) and its level-(n+1) row at p in registers.  Level n+1 is never stored.
 //
 // Face ghosts at level n+1 follow the boundary condition exactly as a single sweep would write them (Dirichlet: the
 // data; Robin: the radiation update from the level-n ghost and its interior neighbour), and the level-(n+2) face
@@ -28,7 +28,8 @@ namespace {
 constexpr int kOX = 120;          // level-(n+2) cells of a tile row
 constexpr int kOW = 8;            // level-(n+2) rows of a tile
 constexpr int kR1 = kOW + 2;      // level-(n+1) rows = consumer warps
-constexpr int kS2 = 4;            // stage ring depth
+constexpr int kS2 = 3;            // stage ring depth
+constexpr int kRing = 4;          // level-(n+1) ring slots (planes p-2 .. p, and one being refilled)
 constexpr int kHX2 = 136;         // staged hi row: cells x0-8 .. x0+127
 constexpr int kLX2 = 144;         // staged lo-code row: cells x0-12 .. x0+131 (a 16-byte-aligned start for 2-byte codes)
 constexpr int kDX2 = 128;         // staged dlt / s row: cells x0-4 .. x0+123
@@ -43,20 +44,20 @@ struct T2 {
     static constexpr int d_off = l_off + align128(l_tx);
     static constexpr int r_off = d_off + d_tx;
     static constexpr int stage = r_off + d_tx;
-    static constexpr int ring_off = kS2 * stage;           // level-(n+1) ring: 3 slots of hi, then 3 slots of lo
+    static constexpr int ring_off = kS2 * stage;           // level-(n+1) ring: kRing slots of hi, then of lo
     static constexpr int ring_slot = kR1 * kDX2;           // floats per slot
-    static constexpr int smem = ring_off + 2 * 3 * ring_slot * 4;
+    static constexpr int smem = ring_off + 2 * kRing * ring_slot * 4;
 };
 
 // Robin coefficients (alpha, beta) of a face ghost, or none
 __device__ __forceinline__ float2 coef(const Bnd& B, int f, long long t) { return B.robin32[B.off[f] + t]; }
 
-__global__ void __launch_bounds__(32 * (kR1 + 1), 2)
+__global__ void __launch_bounds__(32 * kR1, 2)
     k_temporal2_tma(const __grid_constant__ CUtensorMap m_hi, const __grid_constant__ CUtensorMap m_lo,
                     const __grid_constant__ CUtensorMap m_d, const __grid_constant__ CUtensorMap m_s,
                     const SweepArgs A, float* __restrict__ d_out, int* err) {
     extern __shared__ __align__(1024) unsigned char smem[];
-    __shared__ __align__(8) unsigned long long bar_full[kS2], bar_empty[kS2];
+    __shared__ __align__(8) unsigned long long bar_full[kS2];
     const Layout& L = A.L;
     const Bnd& B = A.B;
     const bool robin = B.faces != 0;
@@ -65,36 +66,26 @@ __global__ void __launch_bounds__(32 * (kR1 + 1), 2)
     const int k0 = blockIdx.z * A.zb, k1 = min(L.nz, k0 + A.zb);
     const int nload = k1 - k0 + 3;  // level-n planes k0-1 .. k1+1
 
+    // thread 0 issues the copies: the first kS2 planes now, then plane it+kS2 right after the named barrier of
+    // iteration it (every warp is done with that stage by then, so no "empty" barrier is needed)
+    auto issue = [&](int i) {  // level-n plane k0-1+i into slot i % kS2
+        const uint32_t full = smem_addr(&bar_full[i % kS2]);
+        unsigned char* st = smem + (i % kS2) * T2::stage;
+        const int z = k0 + i;  // padded plane index of plane k0-1+i
+        mbar_expect_tx(full, T2::h_tx + T2::l_tx + 2 * T2::d_tx);
+        tma_load_3d(smem_addr(st + T2::h_off), &m_hi, x0 - 4, j0 - 1, z, full);
+        tma_load_3d(smem_addr(st + T2::l_off), &m_lo, x0 - 8, j0 - 1, z, full);
+        tma_load_3d(smem_addr(st + T2::d_off), &m_d, x0, j0, z, full);
+        tma_load_3d(smem_addr(st + T2::r_off), &m_s, x0, j0, z, full);
+    };
     if (threadIdx.x == 0) {
-        for (int s = 0; s < kS2; ++s) {
-            mbar_init(smem_addr(&bar_full[s]), 1);
-            mbar_init(smem_addr(&bar_empty[s]), kR1);
-        }
+        for (int s = 0; s < kS2; ++s) mbar_init(smem_addr(&bar_full[s]), 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        for (int i = 0; i < kS2 && i < nload; ++i) issue(i);
     }
+    int issued = kS2 < nload ? kS2 : nload;  // tracked by thread 0
     __syncthreads();
-
-    if (warp == kR1) {  // producer
-        if (lane == 0) {
-            int issued = 0;
-            for (int i = 0; i < nload; ++i) {
-                const int s = i % kS2, z = k0 - 1 + i + 1;  // padded plane index of level-n plane k0-1+i
-                if (i >= kS2 && !mbar_wait(smem_addr(&bar_empty[s]), (unsigned)((i / kS2 - 1) & 1), err)) break;
-                const uint32_t full = smem_addr(&bar_full[s]);
-                unsigned char* st = smem + s * T2::stage;
-                mbar_expect_tx(full, T2::h_tx + T2::l_tx + 2 * T2::d_tx);
-                tma_load_3d(smem_addr(st + T2::h_off), &m_hi, x0 - 4, j0 - 1, z, full);
-                tma_load_3d(smem_addr(st + T2::l_off), &m_lo, x0 - 8, j0 - 1, z, full);
-                tma_load_3d(smem_addr(st + T2::d_off), &m_d, x0, j0, z, full);
-                tma_load_3d(smem_addr(st + T2::r_off), &m_s, x0, j0, z, full);
-                issued = i + 1;
-            }
-            for (int i = issued - kS2 > 0 ? issued - kS2 : 0; i < issued; ++i)
-                mbar_wait(smem_addr(&bar_full[i % kS2]), (unsigned)((i / kS2) & 1), err);
-        }
-        return;
-    }
 
     // consumers: warp w computes level n+1 on row j1 = j0-1+w (cells x0-4+4l .. +3) and, for w = 1..8, level n+2 on
     // the same row (lanes 1..30: cells x0 .. x0+119)
@@ -108,7 +99,10 @@ __global__ void __launch_bounds__(32 * (kR1 + 1), 2)
     lo_t* __restrict__ lo_n = (lo_t*)A.lo_n;
     const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
     float* ring_h = (float*)(smem + T2::ring_off);
-    float* ring_l = ring_h + 3 * T2::ring_slot;
+    float* ring_l = ring_h + kRing * T2::ring_slot;
+    auto ring4 = [&](const float* base, int slot, int off) {
+        return *reinterpret_cast<const float4*>(base + slot * T2::ring_slot + off);
+    };
     const int hrow = (warp + 1) * kHX2 + 4 + 4 * lane;  // own group in a stage's hi rows
     const int lrow = (warp + 1) * kLX2 + 8 + 4 * lane;  // ... in its lo-code rows
     const int drow = warp * kDX2 + 4 * lane;            // ... in its dlt / s rows, and in a ring slot
@@ -132,8 +126,7 @@ __global__ void __launch_bounds__(32 * (kR1 + 1), 2)
     float4 hc0 = lds4((const float*)(smem + T2::h_off) + hrow);
     float4 lc0 = lo_decode4(hc0, ldsl4((const lo_t*)(smem + T2::l_off) + lrow));
 
-    float4 m1 = z4, lm1 = z4, c1 = z4, lc1 = z4;  // level n+1, own row: planes p-2, p-1 at iteration p
-    float4 d1c = z4, sc_ = z4;                    // level n+1 increments and the source of plane p-1, own row
+    float4 d1c = z4, sc_ = z4;  // level n+1 increments and the source of plane p-1, own row
 
     const int iters = k1 - k0 + 2;  // level n+1 at planes k0-1 .. k1
     for (int it = 0; it < iters && ok; ++it) {
@@ -160,8 +153,6 @@ __global__ void __launch_bounds__(32 * (kR1 + 1), 2)
             hr = Hc[hrow + 4];
             lr = lo_decode(hr, Lc[lrow + 4]);
         }
-        __syncwarp();
-        if (lane == 0) mbar_arrive(smem_addr(&bar_empty[si]));
 
         // ---- level n+1 at plane p, own row ----
         const bool pl_in = p >= 0 && p < L.nz;
@@ -207,19 +198,32 @@ __global__ void __launch_bounds__(32 * (kR1 + 1), 2)
             set(l1, e, b);
             set(d1, e, c);
         }
-        // publish the row for the neighbouring rows' level n+2
-        float* rh = ring_h + (it % 3) * T2::ring_slot + drow;
-        float* rl = ring_l + (it % 3) * T2::ring_slot + drow;
+        // publish the row (for the neighbouring rows, and as this row's -z / centre planes of the next iterations)
+        float* rh = ring_h + (it % kRing) * T2::ring_slot + drow;
+        float* rl = ring_l + (it % kRing) * T2::ring_slot + drow;
         *reinterpret_cast<float4*>(rh) = h1;
         *reinterpret_cast<float4*>(rl) = l1;
         asm volatile("bar.sync 2, %0;" ::"r"(32 * kR1) : "memory");
+        if (threadIdx.x == 0 && it + kS2 < nload) {  // stage of plane p is free: refill it with plane p+kS2
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            issue(it + kS2);
+            issued = it + kS2 + 1;
+        }
 
         // ---- level n+2 at plane p2 = p-1: from level n+1 planes p-2 (m1), p-1 (c1), p (h1) ----
         const int p2 = p - 1;
+        const int sm1 = (it + kRing - 2) % kRing, sc1 = (it + kRing - 1) % kRing;  // ring slots of planes p-2, p-1
         const bool out_pl = it >= 1 && ((p2 >= k0 && p2 < k1) || (robin && p2 == -1));
-        if (out_pl && warp >= 1 && warp <= kOW) {
-            const float* yh = ring_h + ((it + 2) % 3) * T2::ring_slot;  // slot of iteration it-1
-            const float* yl = ring_l + ((it + 2) % 3) * T2::ring_slot;
+        const bool own_out = out_pl && warp >= 1 && warp <= kOW;
+        float4 c1 = z4, lc1 = z4;
+        if (own_out || (out_pl && row_gy)) {
+            c1 = ring4(ring_h, sc1, drow);
+            lc1 = ring4(ring_l, sc1, drow);
+        }
+        if (own_out) {
+            const float* yh = ring_h + sc1 * T2::ring_slot;
+            const float* yl = ring_l + sc1 * T2::ring_slot;
+            const float4 m1 = ring4(ring_h, sm1, drow), lm1 = ring4(ring_l, sm1, drow);
             const float4 ys = *reinterpret_cast<const float4*>(yh + drow - kDX2);
             const float4 yn = *reinterpret_cast<const float4*>(yh + drow + kDX2);
             const float4 lys = *reinterpret_cast<const float4*>(yl + drow - kDX2);
@@ -282,8 +286,8 @@ __global__ void __launch_bounds__(32 * (kR1 + 1), 2)
         // the y-face ghost rows of level n+2 next to this tile (row -1 in the first row of tiles, row ny in the tile
         // that holds row ny-1), by the warp whose level-(n+1) row is that ghost row
         if (out_pl && row_gy && p2 >= 0 && p2 < L.nz && lane >= 1 && lane <= 30) {
-            const float* yh = ring_h + ((it + 2) % 3) * T2::ring_slot;
-            const float* yl = ring_l + ((it + 2) % 3) * T2::ring_slot;
+            const float* yh = ring_h + sc1 * T2::ring_slot;
+            const float* yl = ring_l + sc1 * T2::ring_slot;
             const int rin = j1 < 0 ? drow + kDX2 : drow - kDX2;  // the interior row next to the ghost row
             const float4 hin = *reinterpret_cast<const float4*>(yh + rin);
             const float4 lin = *reinterpret_cast<const float4*>(yl + rin);
@@ -303,15 +307,19 @@ __global__ void __launch_bounds__(32 * (kR1 + 1), 2)
         lm0 = lc0;
         hc0 = hp0;
         lc0 = lp0;
-        m1 = c1;
-        lm1 = lc1;
-        c1 = h1;
-        lc1 = l1;
         d1c = d1;
         sc_ = s0;
     }
-    // Robin z face at plane nz, by the last chunk: from level n+1 planes nz (c1) and nz-1 (m1)
+    // copies still in flight (only after a wait gave up) must land before the block ends
+    if (threadIdx.x == 0 && !ok)
+        for (int i = issued - kS2 > 0 ? issued - kS2 : 0; i < issued; ++i)
+            mbar_wait(smem_addr(&bar_full[i % kS2]), (unsigned)((i / kS2) & 1), err);
+    // Robin z face at plane nz, by the last chunk: from level n+1 planes nz (c1) and nz-1 (m1), still in the ring
     if (ok && robin && k1 == L.nz && row_in && warp >= 1 && warp <= kOW && lane >= 1 && lane <= 30) {
+        const int last = iters - 1;
+        const float4 c1 = ring4(ring_h, last % kRing, drow), lc1 = ring4(ring_l, last % kRing, drow);
+        const float4 m1 = ring4(ring_h, (last + kRing - 1) % kRing, drow);
+        const float4 lm1 = ring4(ring_l, (last + kRing - 1) % kRing, drow);
         const long long q = L.at(xa, j1, L.nz);
 #pragma unroll
         for (int e = 0; e < 4; ++e)
@@ -363,7 +371,7 @@ int launch_temporal2_tma(hg_grid* g) {
     const int c = g->cur;
     dim3 grid((g->nx + kOX - 1) / kOX, (g->ny + kOW - 1) / kOW, (g->nz + zb - 1) / zb);
     if ((rc = prof_begin(g))) return rc;
-    k_temporal2_tma<<<grid, 32 * (kR1 + 1), T2::smem, g->stream>>>(g->tm2[0 + c], g->tm2[2 + c], g->tm2[4 + g->dcur],
+    k_temporal2_tma<<<grid, 32 * kR1, T2::smem, g->stream>>>(g->tm2[0 + c], g->tm2[2 + c], g->tm2[4 + g->dcur],
                                                                      g->tm2[6], A, (float*)g->dlt[1 - g->dcur],
                                                                      g->derr);
     HG_LAUNCHED("TMA-staged depth-2 sub-step kernel");

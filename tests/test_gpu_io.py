@@ -118,3 +118,17 @@ def test_io_step_rejects_bad_input():
     g.io_step(rho, 2, [np.empty((n, n, n), np.float32) for _ in range(3)])
     g.io_wait(0)
     assert g.stats()["step"] == 2
+
+
+def test_bounded_wait_gives_up_and_is_reported():
+    """A kernel wait that nothing will satisfy ends after its limit; the host sees the timeout and the grid stays
+    usable (no fault, no hang)."""
+    import time
+    g = hg.Grid.unit_cube(24)
+    g.set_density(torch.ones((24, 24, 24), device="cuda"))
+    t0 = time.perf_counter()
+    g.check_bounded_wait()
+    assert time.perf_counter() - t0 < 5.0
+    g.step(4)  # the context and the grid still work, and no error is left pending
+    g.sync()
+    assert g.stats()["step"] == 4
