@@ -517,6 +517,80 @@ def run_adjoint(args):
     return out
 
 
+def poisson_periodic(rho, h, G=1.0):
+    """The discrete periodic Poisson solution of Lap_h phi = 4 pi G (rho - mean rho) for the 7-point Laplacian (its
+    Fourier symbol), zero mean -- the fixed point the sub-steps relax to, used as the reference of --config lag."""
+    import numpy as np
+
+    nz, ny, nx = rho.shape
+    lam = 0.0
+    for ax, n in ((0, nz), (1, ny), (2, nx)):
+        shape = [1, 1, 1]
+        shape[ax] = n
+        lam = lam + (2.0 / (h * h)) * (np.cos(2.0 * np.pi * np.fft.fftfreq(n)).reshape(shape) - 1.0)
+    f = np.fft.fftn(4.0 * np.pi * G * (rho - rho.mean()))
+    lam = np.broadcast_to(lam, f.shape).copy()
+    lam[0, 0, 0] = 1.0
+    f /= lam
+    f[0, 0, 0] = 0.0
+    return np.real(np.fft.ifftn(f))
+
+
+def run_lag(args):
+    """Next row f2: the lag of the hyperbolic potential behind the instantaneous Poisson solution (Sec. 4, Eq. error
+    and Eq. Erreq.: the error is driven by (1/c_h^2) d^2 phi_P / dt^2, so it should fall as (v/c_h)^2), for the
+    orbiting-blob density in a periodic box.  For c_h = k_g v_max, k_g in 5..40, and 2 k_g sub-steps per hydro step
+    (dt_hyd = 0.5 h / v_max), the grid starts on the Poisson solution with its time derivative; after each hydro step
+    phi_H is compared with the Poisson solution of the density at that time (relative L2, both mean-free; the
+    pointwise ratio of Eq. error is undefined where the periodic phi_P crosses zero).  Two source schedules: the
+    density re-evaluated at every sub-step ("smooth", which isolates the c_h lag), and frozen over each hydro step
+    as in Sec. 2 ("frozen", which adds the jump of the source at every hydro step; in a periodic box the waves
+    these jumps launch never leave)."""
+    import numpy as np
+    import torch
+
+    import paper_1602_05700_gb300 as hg
+    from paper_1602_05700_gb300 import inputs as I
+
+    n, M = args.n, args.substeps
+    h, v_max = 1.0 / n, 0.15 * 2.0 * math.pi
+    dt_hyd = 0.5 * h / v_max
+    rho_host = lambda t: I.blob_density(n, I.orbit_blobs(t))  # noqa: E731
+    rho_dev = lambda t: I.blob_density_torch(n, I.orbit_blobs(t), "cuda", torch.float64)  # noqa: E731
+    out = {"workload": f"{n}^3 periodic, two orbiting blobs (sigma 0.05, r 0.15, omega 2pi), {M} hydro steps of "
+                       f"0.5 h / v_max, 2 k_g sub-steps each (nu sqrt 3 = 0.43)",
+           "metric": "mean over the last half of the hydro steps of ||phi_H - phi_P||_2 / ||phi_P||_2", "results": {}}
+    refs = [poisson_periodic(rho_host(m * dt_hyd), h) for m in range(M + 1)]
+    kgs = (5, 10, 20, 40)
+    for kg in kgs:
+        c, nsub = kg * v_max, 2 * kg
+        dt = dt_hyd / nsub
+        row = {}
+        for sched in ("smooth", "frozen"):
+            for prec in ("f32k", "f64"):
+                g = hg.Grid(n, n, n, h, (-0.5, -0.5, -0.5), c, 1.0, dt, prec, "periodic")
+                g.set_phi(torch.from_numpy(refs[0]).cuda(), torch.from_numpy(poisson_periodic(rho_host(-dt), h)).cuda())
+                errs = []
+                for m in range(M):
+                    if sched == "frozen":
+                        g.set_density(rho_dev(m * dt_hyd))
+                        g.step(nsub)
+                    else:
+                        for k in range(nsub):
+                            g.set_density(rho_dev(m * dt_hyd + k * dt))
+                            g.step(1)
+                    phi = g.phi(torch.float64, "cpu")
+                    d = (phi - phi.mean()) - refs[m + 1]
+                    errs.append(float(np.linalg.norm(d) / np.linalg.norm(refs[m + 1])))
+                g.free()
+                row[f"{sched} {prec}"] = float(np.mean(errs[M // 2:]))
+        out["results"][f"k_g={kg}"] = row
+    for key in out["results"][f"k_g={kgs[0]}"]:
+        e = np.log([out["results"][f"k_g={k}"][key] for k in kgs])
+        out[f"slope_log_err_vs_log_kg {key}"] = round(float(np.polyfit(np.log(kgs), e, 1)[0]), 3)
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -533,9 +607,10 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--cpu-substeps", type=int, default=6)
     ap.add_argument("--ref-substeps", type=int, default=1)
-    ap.add_argument("--config", choices=["headline", "precision", "batch", "adjoint"], default="headline",
+    ap.add_argument("--config", choices=["headline", "precision", "batch", "adjoint", "lag"], default="headline",
                     help="headline: the metric's 512^3 line (default); the others print the other workloads")
-    ap.add_argument("--substeps", type=int, default=None, help="sub-steps for --config precision/batch/adjoint")
+    ap.add_argument("--substeps", type=int, default=None,
+                    help="sub-steps for --config precision/batch/adjoint; hydro steps for --config lag")
     args = ap.parse_args()
     from paper_1602_05700_gb300.multi import env_ranks
 
@@ -549,12 +624,12 @@ def main():
     import paper_1602_05700_gb300 as hg
     hg.build()
     if args.config != "headline":
-        defaults = {"precision": (256, 2000), "batch": (0, 500), "adjoint": (128, 400)}
+        defaults = {"precision": (256, 2000), "batch": (0, 500), "adjoint": (128, 400), "lag": (128, 40)}
         n0, t0 = defaults[args.config]
         if args.n == 512 and n0:
             args.n = n0
         args.substeps = args.substeps or t0
-        fn = {"precision": run_precision, "batch": run_batch, "adjoint": run_adjoint}[args.config]
+        fn = {"precision": run_precision, "batch": run_batch, "adjoint": run_adjoint, "lag": run_lag}[args.config]
         if rank == 0:
             print(json.dumps({"config": args.config, **fn(args)}), flush=True)
         return

@@ -369,3 +369,16 @@ def test_adjoint_dot_product(bc):
     lhs = np.sum(phi[1:-1, 1:-1, 1:-1] * mu)
     rhs = np.sum(drho * O.adjoint(g, mu, T))
     assert abs(lhs - rhs) < 1e-11 * max(abs(lhs), 1e-30)
+
+
+def test_periodic_poisson_reference_of_the_lag_study():
+    """The lag study's reference (bench.poisson_periodic) solves the discrete periodic Poisson problem exactly."""
+    import bench
+
+    n, h = 24, 1.0 / 24
+    rho = I.blob_density(n, I.orbit_blobs(0.07))
+    phi = bench.poisson_periodic(rho, h)
+    lap = sum(np.roll(phi, s, a) for a in range(3) for s in (1, -1)) - 6.0 * phi
+    r = lap / h ** 2 - 4.0 * np.pi * (rho - rho.mean())
+    assert np.abs(r).max() <= 1e-12 * np.abs(4.0 * np.pi * rho).max()
+    assert abs(phi.mean()) < 1e-14
