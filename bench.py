@@ -536,6 +536,94 @@ def poisson_periodic(rho, h, G=1.0):
     return np.real(np.fft.ifftn(f))
 
 
+def blob_potential(blobs, x, y, z, G=1.0):
+    """Free-space potential of Gaussian blobs (rows of (cx, cy, cz, sigma, peak)): -G M erf(r / (sqrt(2) sigma)) / r
+    with M = peak (2 pi)^(3/2) sigma^3 -- the continuum solution, used as the boundary data of --config domain."""
+    import numpy as np
+    from scipy.special import erf
+
+    phi = 0.0
+    for cx, cy, cz, sg, a in blobs:
+        m = a * (2.0 * np.pi) ** 1.5 * sg ** 3
+        r = np.sqrt((x - cx) ** 2 + (y - cy) ** 2 + (z - cz) ** 2)
+        phi = phi - G * m * erf(r / (np.sqrt(2.0) * sg)) / r
+    return phi
+
+
+def poisson_dirichlet(rho, ghosts, h, G=1.0):
+    """The discrete Poisson solution Lap_h phi = 4 pi G rho on the interior with the given ghost values (an array of
+    the ghosted shape; only the face ghosts are used), by the sine transform that diagonalises the 7-point Laplacian
+    with Dirichlet data one cell outside the interior."""
+    import numpy as np
+    from scipy.fft import dstn, idstn
+
+    nz, ny, nx = rho.shape
+    f = 4.0 * np.pi * G * rho.astype(np.float64)
+    f[:, :, 0] -= ghosts[1:-1, 1:-1, 0] / h ** 2
+    f[:, :, -1] -= ghosts[1:-1, 1:-1, -1] / h ** 2
+    f[:, 0, :] -= ghosts[1:-1, 0, 1:-1] / h ** 2
+    f[:, -1, :] -= ghosts[1:-1, -1, 1:-1] / h ** 2
+    f[0, :, :] -= ghosts[0, 1:-1, 1:-1] / h ** 2
+    f[-1, :, :] -= ghosts[-1, 1:-1, 1:-1] / h ** 2
+    lam = 0.0
+    for ax, n in ((0, nz), (1, ny), (2, nx)):
+        shape = [1, 1, 1]
+        shape[ax] = n
+        lam = lam + (2.0 / h ** 2) * (np.cos(np.pi * np.arange(1, n + 1) / (n + 1)).reshape(shape) - 1.0)
+    return idstn(dstn(f, type=1) / lam, type=1)
+
+
+def run_domain(args):
+    """Next row f1: the boundary error against the domain size, Robin against multipole Dirichlet, k_g 5 and 20 --
+    a synthetic analogue of the models aD05, aR05 .. cR20 of Sec. 4 (its Table of models).  The orbiting blobs in
+    cubes of side 0.75, 1.5 and 3 at a fixed cell size h = 1/64 (48^3, 96^3, 192^3 cells); the grid starts on the
+    Poisson solution; the density is re-evaluated each hydro step (0.5 h / v_max) and frozen over its 2 k_g
+    sub-steps (Sec. 2).  The reference after each hydro step is the discrete Poisson solution of that density with
+    the free-space potential of the blobs as its boundary data; the error is the paper's average relative error
+    <dphi~> (Eq. error) over the domain."""
+    import numpy as np
+    import torch
+
+    import paper_1602_05700_gb300 as hg
+    from paper_1602_05700_gb300 import inputs as I
+
+    M = args.substeps
+    h, v_max = 1.0 / 64, 0.15 * 2.0 * math.pi
+    dt_hyd = 0.5 * h / v_max
+    out = {"workload": f"orbiting blobs, h = 1/64, domains 0.75 / 1.5 / 3 (48^3 / 96^3 / 192^3), {M} hydro steps of "
+                       "0.5 h / v_max, 2 k_g sub-steps each, source frozen per hydro step",
+           "metric": "<dphi~> of Eq. error against the discrete Poisson solution with free-space boundary data: "
+                     "mean over the last half of the hydro steps / maximum", "results": {}}
+    models = [("aD05", 0.75, "multipole", 5), ("aR05", 0.75, "robin", 5), ("bR05", 1.5, "robin", 5),
+              ("cR05", 3.0, "robin", 5), ("aR20", 0.75, "robin", 20), ("bR20", 1.5, "robin", 20),
+              ("cR20", 3.0, "robin", 20)]
+    refs = {}
+    for side in sorted({m[1] for m in models}):
+        n = int(round(side / h))
+        lo = -0.5 * side
+        cg = lo + (np.arange(-1, n + 1) + 0.5) * h
+        Z, Y, X = np.meshgrid(cg, cg, cg, indexing="ij")
+        def ref(t, n=n, lo=lo, X=X, Y=Y, Z=Z):
+            b = I.orbit_blobs(t)
+            return poisson_dirichlet(I.blob_density(n, b, h=h, lo=lo), blob_potential(b, X, Y, Z), h)
+        refs[side] = (n, lo, ref, [ref(m * dt_hyd) for m in range(M + 1)])
+    for name, side, bc, kg in models:
+        n, lo, ref, rs = refs[side]
+        c, nsub = kg * v_max, 2 * kg
+        dt = dt_hyd / nsub
+        g = hg.Grid(n, n, n, h, (lo, lo, lo), c, 1.0, dt, "f32k", bc, 4 if bc == "multipole" else 0)
+        g.set_density(I.blob_density_torch(n, I.orbit_blobs(0.0), "cuda", torch.float32, h=h, lo=lo))
+        g.set_phi(torch.from_numpy(rs[0]).cuda(), torch.from_numpy(ref(-dt)).cuda())
+        errs = []
+        for m in range(M):
+            g.set_density(I.blob_density_torch(n, I.orbit_blobs(m * dt_hyd), "cuda", torch.float32, h=h, lo=lo))
+            g.step(nsub)
+            errs.append(g.compare(torch.from_numpy(rs[m + 1]).cuda())[2])
+        g.free()
+        out["results"][name] = {"cells": n ** 3, "mean": float(np.mean(errs[M // 2:])), "max": float(np.max(errs))}
+    return out
+
+
 def run_lag(args):
     """Next row f2: the lag of the hyperbolic potential behind the instantaneous Poisson solution (Sec. 4, Eq. error
     and Eq. Erreq.: the error is driven by (1/c_h^2) d^2 phi_P / dt^2, so it should fall as (v/c_h)^2), for the
@@ -607,10 +695,11 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--cpu-substeps", type=int, default=6)
     ap.add_argument("--ref-substeps", type=int, default=1)
-    ap.add_argument("--config", choices=["headline", "precision", "batch", "adjoint", "lag"], default="headline",
+    ap.add_argument("--config", choices=["headline", "precision", "batch", "adjoint", "lag", "domain"],
+                    default="headline",
                     help="headline: the metric's 512^3 line (default); the others print the other workloads")
     ap.add_argument("--substeps", type=int, default=None,
-                    help="sub-steps for --config precision/batch/adjoint; hydro steps for --config lag")
+                    help="sub-steps for --config precision/batch/adjoint; hydro steps for --config lag/domain")
     args = ap.parse_args()
     from paper_1602_05700_gb300.multi import env_ranks
 
@@ -624,12 +713,14 @@ def main():
     import paper_1602_05700_gb300 as hg
     hg.build()
     if args.config != "headline":
-        defaults = {"precision": (256, 2000), "batch": (0, 500), "adjoint": (128, 400), "lag": (128, 40)}
+        defaults = {"precision": (256, 2000), "batch": (0, 500), "adjoint": (128, 400), "lag": (128, 40),
+                    "domain": (0, 40)}
         n0, t0 = defaults[args.config]
         if args.n == 512 and n0:
             args.n = n0
         args.substeps = args.substeps or t0
-        fn = {"precision": run_precision, "batch": run_batch, "adjoint": run_adjoint, "lag": run_lag}[args.config]
+        fn = {"precision": run_precision, "batch": run_batch, "adjoint": run_adjoint, "lag": run_lag,
+              "domain": run_domain}[args.config]
         if rank == 0:
             print(json.dumps({"config": args.config, **fn(args)}), flush=True)
         return

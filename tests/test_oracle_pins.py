@@ -382,3 +382,31 @@ def test_periodic_poisson_reference_of_the_lag_study():
     r = lap / h ** 2 - 4.0 * np.pi * (rho - rho.mean())
     assert np.abs(r).max() <= 1e-12 * np.abs(4.0 * np.pi * rho).max()
     assert abs(phi.mean()) < 1e-14
+
+
+def test_dirichlet_poisson_reference_of_the_domain_study():
+    """The domain study's reference (bench.poisson_dirichlet) solves Lap_h phi = 4 pi G rho with the given face
+    ghosts exactly, and with the free-space boundary data of a blob it approaches the blob's continuum potential."""
+    import bench
+
+    n, h, lo = 20, 1.0 / 20, -0.5
+    rng = np.random.Generator(np.random.PCG64(9))
+    rho = rng.uniform(0.0, 1.0, (n, n, n))
+    ghosts = rng.uniform(-1.0, 0.0, (n + 2, n + 2, n + 2))
+    phi = bench.poisson_dirichlet(rho, ghosts, h)
+    full = ghosts.copy()
+    full[1:-1, 1:-1, 1:-1] = phi
+    lap = sum(np.roll(full, s, a) for a in range(3) for s in (1, -1))[1:-1, 1:-1, 1:-1] - 6.0 * phi
+    assert np.abs(lap / h ** 2 - 4.0 * np.pi * rho).max() <= 1e-10 * 4.0 * np.pi
+    # one Gaussian blob: the discrete solution converges to the continuum potential at second order
+    blobs = I.orbit_blobs(0.0)[:1]
+    errs = []
+    for n in (24, 48):
+        h = 1.0 / n
+        c = lo + (np.arange(-1, n + 1) + 0.5) * h
+        Z, Y, X = np.meshgrid(c, c, c, indexing="ij")
+        exact = bench.blob_potential(blobs, X, Y, Z)
+        phi = bench.poisson_dirichlet(I.blob_density(n, blobs), exact, h)
+        e = exact[1:-1, 1:-1, 1:-1]
+        errs.append(np.linalg.norm(phi - e) / np.linalg.norm(e))
+    assert errs[1] < 2e-3 and errs[0] / errs[1] > 3.5
