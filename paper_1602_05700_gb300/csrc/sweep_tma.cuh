@@ -17,6 +17,7 @@
 #pragma once
 
 #include <cuda.h>
+#include <cuda_pipeline.h>
 
 #include "cell.cuh"
 #include "hg_internal.cuh"
@@ -142,10 +143,12 @@ __device__ __forceinline__ void tma_sweep(const CUtensorMap* m_hi, const CUtenso
         // y faces -- every lane 4 ghosts of row -1 (first row of tiles) and/or row ny (last row of tiles)
         const int w = lane & 15, side = lane >> 4, jx = j0 + w;
         const bool xlane = w < WY && jx < L.ny && (side ? fx1 : fx0);
-        // Robin coefficients of the next face plane, loaded one plane ahead so that their latency stays hidden
-        float2 cx = make_float2(0.f, 0.f), cy[2][4];
+        // Robin coefficients: the x-face ones travel to shared memory by asynchronous copies issued with each plane's
+        // bulk copies (`lag` planes before they are used, so their latency never reaches this warp); the y-face ones
+        // (first and last row of tiles only) are loaded one face plane ahead into registers
+        __shared__ float2 cxs[S][32];
+        float2 cy[2][4];
         auto load_coef = [&](int k) {
-            if (xlane) cx = B.robin32[B.off[side] + (long long)k * L.ny + jx];
 #pragma unroll
             for (int s2 = 0; s2 < 2; ++s2)
 #pragma unroll
@@ -180,10 +183,17 @@ __device__ __forceinline__ void tma_sweep(const CUtensorMap* m_hi, const CUtenso
                 ok = __shfl_sync(0xffffffffu, ok, 0);
                 issued = __shfl_sync(0xffffffffu, issued, 0);
             }
+            if (faces) {  // one copy group per iteration (empty when there is nothing to copy), so counts stay uniform
+                if (xlane && it < planes - 1)
+                    __pipeline_memcpy_async(&cxs[it % S][lane], &B.robin32[B.off[side] + (long long)(k0 + it) * L.ny + jx],
+                                            sizeof(float2));
+                __pipeline_commit();
+            }
             const int pf = it - lag;  // plane (chunk-relative) whose face ghosts are due; the chunk's own planes only
             if (faces && ok && pf >= 0 && pf < planes - 1) {
                 const int s = pf % S, k = k0 + pf;
-                const float2 ax = cx;
+                __pipeline_wait_prior(lag);  // the copy group of plane pf has landed
+                const float2 ax = cxs[s][lane];
                 float2 ay[2][4];
 #pragma unroll
                 for (int s2 = 0; s2 < 2; ++s2)
