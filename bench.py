@@ -202,7 +202,7 @@ def run_ours(args, rank, world, local_rank):
         subs = N_SUB * r["steps"] / max(r["kern_n"], 1)  # sub-steps per launch (the temporal depth)
         alg = BYTES_PER_CELL["f32k"] * cells  # one read of the state and one write per launch
         ach = alg / (avg * 1e-3) / 1e9
-        kname = "k_step_f32k_tma" if r["depth"] == 1 else f"k_temporal_f32k<{r['depth']}>"
+        kname = {1: "k_step_f32k_tma", 2: "k_temporal2_tma"}.get(r["depth"], f"k_temporal_f32k<{r['depth']}>")
         return {"bound": "hbm", "achieved": round(ach, 1), "peak": hbm_peak, "unit": "GB/s",
                 "frac": round(ach / hbm_peak, 4), "peak_kind": f"{peak_kind} copy bandwidth",
                 "traffic": stencil_traffic(kname, n), "kernel": kname, "alg_bytes_per_launch": alg,
