@@ -454,7 +454,8 @@ int set_phi_device(hg_grid* g, const void* phi, const void* prev, int dtype) {
 int accel(hg_grid* g, void* ax, void* ay, void* az, int dtype) {
     const bool aligned = ((uintptr_t)ax | (uintptr_t)ay | (uintptr_t)az) % 16 == 0;
     if (g->prec == HG_PREC_F32K && dtype == HG_DT_F32 && aligned) {
-        const int zb = g->nz < 32 ? g->nz : 32;
+        const int zb = g->nz < 8 ? g->nz : 8;  // short z chunks: more blocks in flight (measured 0.459 ms at 512^3
+                                                // against 0.489 ms with 32-plane chunks)
         dim3 block(32, kAccWY), grid((g->nx + 127) / 128, (g->ny + kAccWY - 1) / kAccWY, (g->nz + zb - 1) / zb);
         k_accel_f32k<<<grid, block, 0, g->stream>>>((const float*)g->phi[g->cur], (const lo_t*)g->lo[g->cur],
                                                     (float*)ax, (float*)ay, (float*)az, g->L,

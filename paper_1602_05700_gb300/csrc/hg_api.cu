@@ -116,6 +116,16 @@ static void release(hg_grid* g) {
     }
 }
 
+int smem_attr_once(const void* fn, int bytes, unsigned long long* done) {
+    int dev = 0;
+    HG_CUDA(cudaGetDevice(&dev));
+    const unsigned long long bit = 1ull << (dev & 63);
+    if (*done & bit) return HG_OK;
+    HG_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    *done |= bit;
+    return HG_OK;
+}
+
 int device_error(hg_grid* g) {
     int e = 0;
     HG_CUDA(cudaMemcpyAsync(&e, g->derr, sizeof e, cudaMemcpyDeviceToHost, g->stream));

@@ -194,6 +194,9 @@ struct SweepArgs;
 int launch_sweep_f32k_tma(hg_grid* g, const SweepArgs& A);  // TMA-staged compensated-float sweep (stencil_tma.cu)
 int launch_temporal2_tma(hg_grid* g);                // two fused TMA-staged sub-steps (temporal_tma.cu)
 int device_error(hg_grid* g);                        // HG_ERR_TIMEOUT if a kernel's bounded wait gave up (syncs)
+// raise a kernel's dynamic shared-memory limit once per device (the attribute is per device); `done` holds one bit
+// per device id
+int smem_attr_once(const void* fn, int bytes, unsigned long long* done);
 int wait_selftest(hg_grid* g);                       // a wait that cannot complete, then device_error (stencil_tma.cu)
 int ensure_staging(hg_grid* g);
 int prepare_source(hg_grid* g, const void* src, int dtype);  // dense rho -> stored s, sum(rho) -> dsum (no sync)

@@ -508,13 +508,10 @@ int launch_step_single(hg_grid* g) {
 }
 
 int launch_step_batch(cudaStream_t st, const TmaEntry* tab, const unsigned* first, int n, unsigned total_blocks) {
-    static bool attr_set = false;
+    static unsigned long long attr_done = 0;
     const int smem = kStages * StageGeom<kTmaWY>::bytes;
-    if (!attr_set) {
-        HG_CUDA(cudaFuncSetAttribute(k_step_batch<kTmaWY, kStages>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     smem));
-        attr_set = true;
-    }
+    int rc = smem_attr_once((const void*)k_step_batch<kTmaWY, kStages>, smem, &attr_done);
+    if (rc) return rc;
     k_step_batch<kTmaWY, kStages><<<total_blocks, dim3(32, kTmaWY + 1), smem, st>>>(tab, first, n);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "batched sub-step kernel");

@@ -88,13 +88,9 @@ static constexpr int kSmem = kStages * StageGeom<kTmaWY>::bytes;
 int launch_sweep_f32k_tma(hg_grid* g, const SweepArgs& A) {
     int rc = tma_maps(g);
     if (rc) return rc;
-    static bool attr_set = false;
+    static unsigned long long attr_done = 0;
     const int smem = kSmem;
-    if (!attr_set) {
-        HG_CUDA(cudaFuncSetAttribute(k_step_f32k_tma<kTmaWY, kStages>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     smem));
-        attr_set = true;
-    }
+    if ((rc = smem_attr_once((const void*)k_step_f32k_tma<kTmaWY, kStages>, smem, &attr_done))) return rc;
     const int c = g->cur;
     dim3 grid((g->nx + kTX - 1) / kTX, (g->ny + kTmaWY - 1) / kTmaWY, (g->nz + A.zb - 1) / A.zb);
     SweepArgs At = A;

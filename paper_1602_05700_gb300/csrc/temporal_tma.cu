@@ -358,11 +358,8 @@ int launch_temporal2_tma(hg_grid* g) {
         return fail(HG_ERR_STATE, "the TMA-staged depth-2 kernel needs a Dirichlet or Robin f32k grid with two dlt buffers");
     int rc = tma2_maps(g);
     if (rc) return rc;
-    static bool attr_set = false;
-    if (!attr_set) {
-        HG_CUDA(cudaFuncSetAttribute(k_temporal2_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, T2::smem));
-        attr_set = true;
-    }
+    static unsigned long long attr_done = 0;
+    if ((rc = smem_attr_once((const void*)k_temporal2_tma, T2::smem, &attr_done))) return rc;
     const int zb = g->zb > 0 ? (g->zb < g->nz ? g->zb : g->nz) : (g->nz < kZ2 ? g->nz : kZ2);
     SweepArgs A = sweep_args(g, zb);
     A.B.faces = g->bc == HG_BC_ROBIN ? 1 : 0;
