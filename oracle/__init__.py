@@ -10,6 +10,11 @@ Every function here is pinned by ``tests/test_oracle_pins.py`` against something
 Poisson solve, the exact discrete plane wave, the Green's-function sum, the analytic sphere, the spherical
 harmonic addition theorem, a sparse direct solve with the Robin relation, central finite differences).
 
+The hydrodynamics that consumes -grad phi (paper Sec. 2: finite volume, HLLC, gamma = 5/3, outgoing boundaries)
+lives in ``hydro_oracle.c`` and is wrapped by the ``hydro_*`` functions below; ``tests/test_hydro_pins.py`` pins
+it against the exact Riemann solution, exact contact preservation, conservation, axis-permutation symmetry, the
+exact momentum and energy response to a uniform field, and the polytrope's virial theorem.
+
 Arrays: a *ghosted* array has shape (nz+2, ny+2, nx+2) with the interior at [1:-1, 1:-1, 1:-1]; an *interior*
 array has shape (nz, ny, nx).  Only face ghosts are meaningful; edge and corner ghosts stay zero.
 """
@@ -27,19 +32,19 @@ BC_ROBIN = 1
 BC_PERIODIC = 2
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = os.path.join(_HERE, "hg_oracle.c")
+_SRCS = [os.path.join(_HERE, "hg_oracle.c"), os.path.join(_HERE, "hydro_oracle.c")]
 _LIB_DIR = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_LIB_DIR, "libhgoracle.so")
 
 
 def build(force: bool = False) -> str:
-    """Compile hg_oracle.c with gcc (-O2, no FMA contraction, no fast-math) into oracle/_build/."""
-    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
+    """Compile the oracle's C files with gcc (-O2, no FMA contraction, no fast-math) into oracle/_build/."""
+    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= max(os.path.getmtime(f) for f in _SRCS):
         return _LIB
     os.makedirs(_LIB_DIR, exist_ok=True)
     tmp = _LIB + f".tmp{os.getpid()}"
     subprocess.check_call(["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
-                           "-o", tmp, _SRC, "-lm"])
+                           "-o", tmp, *_SRCS, "-lm"])
     os.replace(tmp, _LIB)
     return _LIB
 
@@ -48,6 +53,11 @@ class _OgGrid(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int), ("bc", ctypes.c_int),
                 ("h", ctypes.c_double), ("x0", ctypes.c_double), ("y0", ctypes.c_double), ("z0", ctypes.c_double),
                 ("c", ctypes.c_double), ("G", ctypes.c_double), ("dt", ctypes.c_double)]
+
+
+class _OhGrid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int), ("h", ctypes.c_double),
+                ("gamma", ctypes.c_double), ("rho_floor", ctypes.c_double), ("p_floor", ctypes.c_double)]
 
 
 _lib = None
@@ -78,6 +88,15 @@ def _L():
         lib.og_residual.argtypes = [gp, dp, dp, dp]
         lib.og_compare.argtypes = [gp, dp, dp, dp]
         lib.og_adjoint.argtypes = [gp, dp, ctypes.c_int, dp]
+        hp = P(_OhGrid)
+        lib.oh_cons_from_prim.argtypes = [hp, dp, dp]
+        lib.oh_prim_from_cons.argtypes = [hp, dp, dp]
+        lib.oh_hllc.argtypes = [d, dp, dp, ctypes.c_int, dp]
+        lib.oh_residual.argtypes = [hp, dp, ctypes.c_void_p, dp]
+        lib.oh_step.argtypes = [hp, dp, ctypes.c_void_p, d, dp]
+        lib.oh_max_speed.restype = d
+        lib.oh_max_speed.argtypes = [hp, dp]
+        lib.oh_virial.argtypes = [hp, dp, dp, dp]
         _lib = lib
     return _lib
 
@@ -242,3 +261,93 @@ def initial_state(g: Grid, rho: np.ndarray, lmax: int = 0, phi0: np.ndarray | No
         fill_robin_static_ghosts(g, phi)
         fill_robin_static_ghosts(g, prev)
     return phi, prev
+
+
+# ---- hydrodynamics consuming -grad phi (paper Sec. 2) ------------------------------------------------------------
+
+@dataclass
+class HydroGrid:
+    """nx*ny*nz cells of side h for the ideal-gas hydrodynamics; fields are (5, nz, ny, nx) float64 arrays of
+    conserved (rho, mx, my, mz, E) or primitive (rho, vx, vy, vz, P) variables."""
+    nx: int
+    ny: int
+    nz: int
+    h: float
+    gamma: float = 5.0 / 3.0
+    rho_floor: float = 0.0
+    p_floor: float = 0.0
+
+    def _s(self) -> _OhGrid:
+        return _OhGrid(self.nx, self.ny, self.nz, self.h, self.gamma, self.rho_floor, self.p_floor)
+
+    @property
+    def shape(self):
+        return (self.nz, self.ny, self.nx)
+
+
+def _fields(hg: HydroGrid, a, planes: int = 5) -> np.ndarray:
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    assert a.shape == (planes,) + hg.shape, a.shape
+    return a
+
+
+def hydro_cons(hg: HydroGrid, W) -> np.ndarray:
+    W = _fields(hg, W)
+    U = np.zeros_like(W)
+    _L().oh_cons_from_prim(ctypes.byref(hg._s()), _p(W), _p(U))
+    return U
+
+
+def hydro_prim(hg: HydroGrid, U) -> np.ndarray:
+    U = _fields(hg, U)
+    W = np.zeros_like(U)
+    _L().oh_prim_from_cons(ctypes.byref(hg._s()), _p(U), _p(W))
+    return W
+
+
+def hydro_hllc(gamma: float, wl, wr, d: int) -> np.ndarray:
+    """HLLC flux along axis d (0 = x) between primitive states wl and wr (5 values each)."""
+    wl = np.ascontiguousarray(wl, dtype=np.float64)
+    wr = np.ascontiguousarray(wr, dtype=np.float64)
+    F = np.zeros(5)
+    _L().oh_hllc(gamma, _p(wl), _p(wr), int(d), _p(F))
+    return F
+
+
+def hydro_residual(hg: HydroGrid, U, A=None) -> np.ndarray:
+    """L(U) = -div F / h + S(U); A = (ax, ay, az) or None."""
+    U = _fields(hg, U)
+    L = np.zeros_like(U)
+    Ap = None if A is None else _fields(hg, A, 3)
+    _L().oh_residual(ctypes.byref(hg._s()), _p(U), None if Ap is None else _p(Ap), _p(L))
+    return L
+
+
+def hydro_step(hg: HydroGrid, U: np.ndarray, dt: float, A=None) -> None:
+    """One two-stage hydro step of dt, in place on the conserved fields U."""
+    assert U.dtype == np.float64 and U.flags.c_contiguous and U.shape == (5,) + hg.shape
+    Ap = None if A is None else _fields(hg, A, 3)
+    work = np.zeros((10,) + hg.shape)
+    _L().oh_step(ctypes.byref(hg._s()), _p(U), None if Ap is None else _p(Ap), float(dt), _p(work))
+
+
+def hydro_max_speed(hg: HydroGrid, U) -> float:
+    return _L().oh_max_speed(ctypes.byref(hg._s()), _p(_fields(hg, U)))
+
+
+def hydro_virial(hg: HydroGrid, U, phi) -> dict:
+    """The paper's virial measure over bound cells; phi is an interior (nz, ny, nx) array."""
+    phi = np.ascontiguousarray(phi, dtype=np.float64)
+    assert phi.shape == hg.shape
+    out = np.zeros(6)
+    _L().oh_virial(ctypes.byref(hg._s()), _p(_fields(hg, U)), _p(phi), _p(out))
+    return dict(W=out[0], U=out[1], K=out[2], VC=out[3], rho_max=out[4], M_bound=out[5])
+
+
+def coupled_step(og: Grid, phi: np.ndarray, phi_prev: np.ndarray, hg: HydroGrid, U: np.ndarray, dt: float,
+                 n_sub: int) -> None:
+    """One hydro step with self-gravity (Sec. 2): the wave equation advanced n_sub sub-steps with rho = U[0] held
+    fixed, then the hydro step of dt with a = -grad phi of the advanced potential (both in place)."""
+    run(og, phi, phi_prev, U[0], n_sub)
+    A = np.stack(accel(og, phi))
+    hydro_step(hg, U, dt, A)

@@ -13,6 +13,11 @@ Recipes (unit cube [-1/2, 1/2]^3, N cells per side, cell-centred):
   orbit        two blobs of sigma 0.05 and mass 1 each (peak 1/((2 pi)^{3/2} sigma^3)) at +-0.15 on a circle in
                the z = 0 plane, angle omega t with omega = 2 pi.
   noise        i.i.d. uniform values for stencil-parity inputs (the stencil is checked on arbitrary data).
+  polytrope    the 3D star of the paper's virial test (Sec. 2): a Lane-Emden polytrope of index n (default 3)
+               with mass M and radius R at the origin, point-sampled at cell centres, v = 0, P = K rho^(1+1/n),
+               a dilute atmosphere (rho = atm * rho_c, P from the same K) outside, optional i.i.d. relative
+               density perturbations inside the star, and its exact potential for seeding phi.
+  hydro states primitive fields (rho, vx, vy, vz, P): shock tubes along an axis and i.i.d. bounded noise.
 """
 from __future__ import annotations
 
@@ -138,3 +143,118 @@ def blob_density_torch(nx: int, blobs: np.ndarray, device, dtype, ny: int | None
         ez = torch.exp(-((zs - czb) ** 2) / (2 * s * s))
         rho += (a * ez[:, None, None] * ey[None, :, None] * ex[None, None, :]).to(dtype)
     return rho
+
+
+def lane_emden(n: float, dxi: float = 1e-3):
+    """Lane-Emden function of index n: (1/xi^2) d/dxi (xi^2 dtheta/dxi) = -theta^n, theta(0) = 1, theta'(0) = 0.
+
+    Classical RK4 in (theta, theta') with step dxi from the series start theta = 1 - xi^2/6 + n xi^4/120 at
+    xi = dxi, up to the first zero xi_1 (refined by Newton steps on the last RK4 step), or to xi = 20 when there is
+    none (n >= 5).  Returns (xi, theta, dtheta, xi1, omega) with omega = -xi1^2 theta'(xi1) (nan without a zero).
+    """
+    def rhs(x, t, dt):
+        return dt, -(max(t, 0.0) ** n) - 2.0 * dt / x
+
+    x = dxi
+    t = 1.0 - x * x / 6.0 + n * x ** 4 / 120.0
+    d = -x / 3.0 + n * x ** 3 / 30.0
+    xs, ts, ds = [0.0, x], [1.0, t], [0.0, d]
+
+    def rk4(x, t, d, hh):
+        k1 = rhs(x, t, d)
+        k2 = rhs(x + hh / 2, t + hh / 2 * k1[0], d + hh / 2 * k1[1])
+        k3 = rhs(x + hh / 2, t + hh / 2 * k2[0], d + hh / 2 * k2[1])
+        k4 = rhs(x + hh, t + hh * k3[0], d + hh * k3[1])
+        return (t + hh / 6 * (k1[0] + 2 * k2[0] + 2 * k3[0] + k4[0]),
+                d + hh / 6 * (k1[1] + 2 * k2[1] + 2 * k3[1] + k4[1]))
+
+    while x < 20.0:
+        tn, dn = rk4(x, t, d, dxi)
+        if tn <= 0.0:
+            hh = -t / d
+            for _ in range(4):  # Newton on theta(x + hh) = 0 along the RK4 step
+                tz, dz = rk4(x, t, d, hh)
+                hh -= tz / dz
+            tz, dz = rk4(x, t, d, hh)
+            xs.append(x + hh)
+            ts.append(0.0)
+            ds.append(dz)
+            xi1 = x + hh
+            return np.array(xs), np.array(ts), np.array(ds), xi1, -xi1 * xi1 * dz
+        x, t, d = x + dxi, tn, dn
+        xs.append(x)
+        ts.append(t)
+        ds.append(d)
+    return np.array(xs), np.array(ts), np.array(ds), float("nan"), float("nan")
+
+
+def _hermite(xs, ts, ds, x):
+    """Cubic Hermite interpolation of theta from the RK4 table (values and derivatives) at points x <= xs[-1]."""
+    x = np.asarray(x, dtype=np.float64)
+    k = np.clip(np.searchsorted(xs, x, side="right") - 1, 0, len(xs) - 2)
+    x0, x1 = xs[k], xs[k + 1]
+    w = x1 - x0
+    s = (x - x0) / w
+    h00 = (1 + 2 * s) * (1 - s) ** 2
+    h10 = s * (1 - s) ** 2
+    h01 = s * s * (3 - 2 * s)
+    h11 = s * s * (s - 1)
+    return h00 * ts[k] + h10 * w * ds[k] + h01 * ts[k + 1] + h11 * w * ds[k + 1]
+
+
+def polytrope(nx: int, n_index: float = 3.0, mass: float = 1.0, radius: float = 1.0 / 3.0, G: float = 1.0,
+              atm: float = 1e-6, pert: float = 0.0, seed: int = 0, ny: int | None = None, nz: int | None = None,
+              h: float | None = None, lo: float = -0.5):
+    """Polytropic star at the origin: returns (rho, P, phi, info), each field (nz, ny, nx) float64.
+
+    rho = rho_c theta^n(r / alpha) with alpha = R / xi_1 and rho_c = M / (4 pi alpha^3 omega); P = K rho^(1+1/n)
+    with K = 4 pi G alpha^2 rho_c^(1-1/n) / (n+1); exact potential -G M / R - (n+1) K rho_c^(1/n) theta inside,
+    -G M / r outside.  Outside the star (and wherever rho_c theta^n < atm rho_c) rho = atm rho_c, P = K rho^(1+1/n).
+    pert > 0 multiplies rho inside the star by 1 + pert u, u ~ U[-1, 1] from PCG64(seed) (P is left unchanged).
+    """
+    ny = ny or nx
+    nz = nz or nx
+    h = 1.0 / nx if h is None else h
+    xs_, ts_, ds_, xi1, omega = lane_emden(n_index)
+    alpha = radius / xi1
+    rho_c = mass / (4.0 * np.pi * alpha ** 3 * omega)
+    K = 4.0 * np.pi * G * alpha ** 2 * rho_c ** (1.0 - 1.0 / n_index) / (n_index + 1.0)
+    x = cell_centres_1d(nx, lo, h)
+    y = cell_centres_1d(ny, lo, h)
+    z = cell_centres_1d(nz, lo, h)
+    r = np.sqrt(z[:, None, None] ** 2 + y[None, :, None] ** 2 + x[None, None, :] ** 2)
+    inside = r < radius
+    theta = np.zeros_like(r)
+    theta[inside] = np.maximum(_hermite(xs_, ts_, ds_, r[inside] / alpha), 0.0)
+    rho_atm = atm * rho_c
+    rho = np.maximum(rho_c * theta ** n_index, rho_atm)
+    if pert > 0.0:
+        u = noise(r.shape, seed, -1.0, 1.0)
+        rho = np.where(inside & (rho > rho_atm), rho * (1.0 + pert * u), rho)
+    P = K * np.maximum(rho_c * theta ** n_index, rho_atm) ** (1.0 + 1.0 / n_index)
+    phi = np.where(inside, -G * mass / radius - (n_index + 1.0) * K * rho_c ** (1.0 / n_index) * theta,
+                   -G * mass / np.maximum(r, 1e-300))
+    info = dict(rho_c=rho_c, K=K, alpha=alpha, xi1=xi1, omega=omega, rho_atm=rho_atm,
+                p_atm=K * rho_atm ** (1.0 + 1.0 / n_index))
+    return rho, P, phi, info
+
+
+def shock_tube(shape, axis: int, left=(1.0, 0.0, 1.0), right=(0.125, 0.0, 0.1), frac: float = 0.5):
+    """Primitive fields (5, nz, ny, nx) of a Riemann problem along axis (0 = x, 1 = y, 2 = z): (rho, u_n, P) on
+    the cells below frac of the axis length, the right triple above, transverse velocities zero."""
+    nz, ny, nx = shape
+    n = (nx, ny, nz)[axis]
+    side = (np.arange(n) + 0.5) < frac * n
+    W = np.zeros((5,) + tuple(shape))
+    for q, (a, b) in ((0, (left[0], right[0])), (1 + axis, (left[1], right[1])), (4, (left[2], right[2]))):
+        line = np.where(side, a, b)
+        W[q] = line.reshape([(n if ax == axis else 1) for ax in (2, 1, 0)])
+    return W
+
+
+def hydro_noise(shape, seed: int, drho=0.5, dv=0.3, dp=0.5):
+    """Primitive fields (5, nz, ny, nx): rho = 1 + drho u, v_i = dv u, P = 1 + dp u with independent i.i.d.
+    u ~ U[-1, 1] (PCG64 from seed)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    u = rng.uniform(-1.0, 1.0, size=(5,) + tuple(shape))
+    return np.stack([1.0 + drho * u[0], dv * u[1], dv * u[2], dv * u[3], 1.0 + dp * u[4]])
