@@ -679,6 +679,97 @@ def run_lag(args):
     return out
 
 
+def run_virial(args):
+    """The paper's 3D star (Sec. 2; Sec. 3, Eq. VC): an n = 3 polytrope (M = 1, R = 1/3, G = 1) at the centre of
+    [-1/2, 1/2]^3 on N^3 cells (the paper's 140^3 octant of a domain 1.5 R wide, mirrored: N = 280), gamma = 5/3, a
+    dilute atmosphere of 1e-6 rho_c, evolved by the coupled GPU step (FP32 hydro, compensated-FP32 gravity, Robin
+    boundary) for `substeps` hydro steps with k_g = 5 and Courant number 0.3 for both parts (c_g fixed from the
+    initial max(c_s + |v|); each hydro step the largest multiple of the gravity sub-step within its own Courant
+    limit); unperturbed and with 1% random density perturbations.  Reports VC and rho_max / rho_max(0) against
+    time, and the time of a coupled hydro step split into its gravity and hydro parts."""
+    import numpy as np
+    import torch
+
+    import paper_1602_05700_gb300 as hg
+    from paper_1602_05700_gb300 import inputs as I
+
+    n, steps, kg, cfl = args.n, args.substeps, 5.0, 0.3
+    h = 1.0 / n
+    t_dyn = (1.0 / 3.0) ** 1.5  # sqrt(R^3 / (G M))
+    res = {"workload": f"{n}^3 n=3 polytrope (M 1, R 1/3), gamma 5/3, Robin gravity, k_g {kg:g}, Courant {cfl:g}, "
+                       f"{steps} hydro steps", "t_dyn": t_dyn}
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    for label, pert in (("unperturbed", 0.0), ("perturbed_1pct", 0.01)):
+        rho, P, phi, info = I.polytrope(n, pert=pert, seed=21)
+        W = np.zeros((5, n, n, n), np.float32)
+        W[0], W[4] = rho, P
+        H = hg.Hydro(n, n, n, h, 5.0 / 3.0, 0.5 * info["rho_atm"], 0.5 * info["p_atm"], dtype="f32")
+        H.set_primitive(torch.from_numpy(W).cuda())
+        del W
+        s0 = H.max_speed()
+        c = kg * s0
+        dtg = cfl * h / (c * np.sqrt(3.0))
+        g = hg.Grid(n, n, n, h, (-0.5, -0.5, -0.5), c, 1.0, dtg, "f32k", "robin")
+        g.set_phi(torch.from_numpy(phi).cuda())
+        v0 = H.virial(g)
+        trace = [(0.0, v0["VC"], 1.0)]
+        t, nsub, wall = 0.0, None, 0.0
+        every = max(1, steps // 40)
+        e0, e1 = ev(), ev()
+        for it in range(steps):
+            if it % 10 == 0:
+                nsub = max(1, int(np.floor(cfl * h / H.max_speed() / dtg)))
+            e0.record()
+            H.step(nsub * dtg, g, nsub)
+            e1.record()
+            t += nsub * dtg
+            if (it + 1) % every == 0:
+                torch.cuda.synchronize()
+                wall += e0.elapsed_time(e1)
+                v = H.virial(g)
+                trace.append((round(t / t_dyn, 4), v["VC"], v["rho_max"] / v0["rho_max"]))
+        vc = np.array([r[1] for r in trace])
+        res[label] = {"t_end_over_t_dyn": round(t / t_dyn, 3), "substeps_per_hydro_step": nsub,
+                      "VC_initial": trace[0][1], "VC_final": trace[-1][1],
+                      "VC_max_abs": float(np.abs(vc).max()), "VC_max_abs_after_1_t_dyn":
+                      float(max((abs(r[1]) for r in trace if r[0] >= 1.0), default=float("nan"))),
+                      "rho_max_ratio_final": trace[-1][2], "trace_t_VC_rhomax": trace[::4] + [trace[-1]]}
+        if label == "unperturbed":
+            # time split of one coupled step: the whole step, its gravity part, and the hydro stages alone
+            torch.cuda.synchronize()
+            reps = 20
+            dt = nsub * dtg
+
+            def timed(fn):
+                a, b = ev(), ev()
+                fn()
+                torch.cuda.synchronize()
+                a.record()
+                for _ in range(reps):
+                    fn()
+                b.record()
+                torch.cuda.synchronize()
+                return a.elapsed_time(b) / reps
+
+            ms_step = timed(lambda: H.step(dt, g, nsub))
+            rho_d = H.state()[0].contiguous()
+            ms_grav = timed(lambda: (g.set_density(rho_d), g.step(nsub), g.accel()))
+            ms_hyd = timed(lambda: H.step(dt))
+            alg = 50 * n ** 3  # bytes per stage launch without gravity: avg of (5 read + 5 write) and (10 + 5) floats
+            pk, kind = peaks()
+            res["timing"] = {"ms_per_coupled_step": round(ms_step, 4), "ms_gravity_substeps_and_accel": round(ms_grav, 4),
+                             "ms_hydro_two_stages": round(ms_hyd, 4),
+                             "gcell_hydro_steps_per_s": round(n ** 3 / (ms_step * 1e-3) / 1e9, 3),
+                             "hydro_stage_roofline": {"bound": "hbm", "kernel": "k_hydro_stage<float>",
+                                                      "achieved": round(alg / (ms_hyd / 2 * 1e-3) / 1e9, 1),
+                                                      "peak": pk, "unit": "GB/s",
+                                                      "frac": round(alg / (ms_hyd / 2 * 1e-3) / 1e9 / pk, 4),
+                                                      "peak_kind": kind, "alg_bytes_per_launch": alg}}
+        g.free()
+        H.free()
+    return res
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -695,11 +786,11 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--cpu-substeps", type=int, default=6)
     ap.add_argument("--ref-substeps", type=int, default=1)
-    ap.add_argument("--config", choices=["headline", "precision", "batch", "adjoint", "lag", "domain"],
+    ap.add_argument("--config", choices=["headline", "precision", "batch", "adjoint", "lag", "domain", "virial"],
                     default="headline",
                     help="headline: the metric's 512^3 line (default); the others print the other workloads")
     ap.add_argument("--substeps", type=int, default=None,
-                    help="sub-steps for --config precision/batch/adjoint; hydro steps for --config lag/domain")
+                    help="sub-steps for --config precision/batch/adjoint; hydro steps for --config lag/domain/virial")
     args = ap.parse_args()
     from paper_1602_05700_gb300.multi import env_ranks
 
@@ -714,13 +805,13 @@ def main():
     hg.build()
     if args.config != "headline":
         defaults = {"precision": (256, 2000), "batch": (0, 500), "adjoint": (128, 400), "lag": (128, 40),
-                    "domain": (0, 40)}
+                    "domain": (0, 40), "virial": (280, 1900)}
         n0, t0 = defaults[args.config]
         if args.n == 512 and n0:
             args.n = n0
         args.substeps = args.substeps or t0
         fn = {"precision": run_precision, "batch": run_batch, "adjoint": run_adjoint, "lag": run_lag,
-              "domain": run_domain}[args.config]
+              "domain": run_domain, "virial": run_virial}[args.config]
         if rank == 0:
             print(json.dumps({"config": args.config, **fn(args)}), flush=True)
         return

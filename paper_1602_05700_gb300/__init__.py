@@ -8,6 +8,13 @@ step of the method runs in the CUDA kernels of ``csrc/``; PyTorch only provides 
     g.set_density(rho)           # (nz, ny, nx) tensor or array, rho frozen over the sub-steps (Sec. 2)
     g.step(20)                   # k_g wave sub-steps per hydro step (Sec. 2)
     ax, ay, az = g.accel()       # -grad phi for the hydro step
+
+The hydrodynamics that consumes it (Sec. 2: finite volume, HLLC, gamma = 5/3, outgoing boundaries) is ``Hydro``:
+
+    H = hg.Hydro(g.nx, g.ny, g.nz, g.h, dtype="f32")
+    H.set_primitive(W)           # (5, nz, ny, nx): rho, vx, vy, vz, P
+    H.step(dt, g, n_sub)         # rho -> g, n_sub wave sub-steps, -grad phi, two Runge-Kutta stages
+    H.virial(g)                  # the paper's VC over bound cells
 """
 from __future__ import annotations
 
@@ -24,7 +31,7 @@ BC = {"dirichlet": HG_BC_DIRICHLET_ANALYTIC, "dirichlet_analytic": HG_BC_DIRICHL
       "robin": HG_BC_ROBIN, "periodic": HG_BC_PERIODIC}
 PREC = {"f32k": HG_PREC_F32K, "f64": HG_PREC_F64}
 
-__all__ = ["Grid", "Batch", "HGError", "BC", "PREC", "build"]
+__all__ = ["Grid", "Batch", "Hydro", "HGError", "BC", "PREC", "build"]
 
 
 def build(force: bool = False) -> str:
@@ -325,6 +332,91 @@ class Batch:
     def free(self):
         if getattr(self, "_h", None) is not None:
             _lib.lib().hg_batch_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+HYDRO_DT = {"f32": HG_DT_F32, "f64": HG_DT_F64}
+
+
+class Hydro:
+    """Ideal-gas hydro state on nx*ny*nz cells of side h (include/hg_hydro.h): conserved (rho, mx, my, mz, E) in
+    5 planes, stepped with the gravity of a matching Grid on the same stream."""
+
+    def __init__(self, nx, ny, nz, h, gamma=5.0 / 3.0, rho_floor=0.0, p_floor=0.0, dtype="f32", stream=None):
+        torch = _torch()
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self._stream = stream
+        self.dtype = HYDRO_DT[dtype] if isinstance(dtype, str) else int(dtype)
+        handle = ctypes.c_void_p()
+        _lib.check(_lib.lib().hg_hydro_init(ctypes.byref(handle), int(nx), int(ny), int(nz), float(h), float(gamma),
+                                            float(rho_floor), float(p_floor), self.dtype,
+                                            ctypes.c_void_p(stream.cuda_stream)))
+        self._h = handle
+        self.nx, self.ny, self.nz, self.h, self.gamma = int(nx), int(ny), int(nz), float(h), float(gamma)
+        self.device = torch.device("cuda", torch.cuda.current_device())
+
+    @property
+    def shape(self):
+        return (5, self.nz, self.ny, self.nx)
+
+    @property
+    def handle(self):
+        if self._h is None:
+            raise HGError(-1, "hydro state was freed")
+        return self._h
+
+    def _fields(self, x):
+        p, code, dev, keep = _buffer(x)
+        n = keep.numel() if hasattr(keep, "numel") else keep.size
+        if n != 5 * self.nx * self.ny * self.nz:
+            raise HGError(-1, f"field set has {n} values, expected 5 x {self.nx * self.ny * self.nz}")
+        return p, code, dev, keep
+
+    def set_primitive(self, W):
+        p, code, dev, keep = self._fields(W)
+        _lib.check(_lib.lib().hg_hydro_set_primitive(self.handle, p, code, dev))
+
+    def set_state(self, U):
+        p, code, dev, keep = self._fields(U)
+        _lib.check(_lib.lib().hg_hydro_set_state(self.handle, p, code, dev))
+
+    def state(self, device="cuda"):
+        torch = _torch()
+        t = torch.empty(self.shape, dtype=torch.float64 if self.dtype == HG_DT_F64 else torch.float32,
+                        device=self.device if device == "cuda" else "cpu")
+        _lib.check(_lib.lib().hg_hydro_get_state(self.handle, ctypes.c_void_p(t.data_ptr()), self.dtype,
+                                                 1 if t.is_cuda else 0))
+        return t
+
+    def max_speed(self) -> float:
+        s = ctypes.c_double()
+        _lib.check(_lib.lib().hg_hydro_max_speed(self.handle, ctypes.byref(s)))
+        return s.value
+
+    def step(self, dt, grid=None, n_sub=0):
+        _lib.check(_lib.lib().hg_hydro_step(self.handle, grid.handle if grid is not None else None, float(dt),
+                                            int(n_sub)))
+
+    def virial(self, grid) -> dict:
+        out = (ctypes.c_double * 6)()
+        _lib.check(_lib.lib().hg_hydro_virial(self.handle, grid.handle, out))
+        return dict(W=out[0], U=out[1], K=out[2], VC=out[3], rho_max=out[4], M_bound=out[5])
+
+    def launches(self) -> int:
+        n = ctypes.c_longlong()
+        _lib.check(_lib.lib().hg_hydro_launches(self.handle, ctypes.byref(n)))
+        return n.value
+
+    def free(self):
+        if getattr(self, "_h", None) is not None:
+            _lib.lib().hg_hydro_free(self._h)
             self._h = None
 
     def __del__(self):

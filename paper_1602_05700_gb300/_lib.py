@@ -1,4 +1,4 @@
-"""ctypes declarations of the C ABI in include/hg.h (argument marshalling only).
+"""ctypes declarations of the C ABI in include/hg.h and include/hg_hydro.h (argument marshalling only).
 
 The library is loaded from paper_1602_05700_gb300/_build/libhypergrav.so.  There is no other implementation:
 if the library is missing, every call raises.
@@ -48,7 +48,7 @@ _I = ctypes.c_int
 _D = ctypes.c_double
 _P = ctypes.POINTER
 
-# name -> (restype, argtypes); the exported symbols of include/hg.h
+# name -> (restype, argtypes); the exported symbols of include/hg.h and include/hg_hydro.h
 SIGNATURES = {
     "hg_init_grid": (_I, [_P(_V), _I, _I, _I, _D, _P(_D), _D, _D, _D, _I, _I, _I, _V]),
     "hg_set_density": (_I, [_V, _V, _I, _I]),
@@ -82,6 +82,16 @@ SIGNATURES = {
     "hg_batch_free": (None, [_V]),
     "hg_moments_noalloc": (_I, [_V, _I, _I, _I, _I, _D, _P(_D), _I, _V, _I, _V]),
     "hg_last_error": (ctypes.c_char_p, []),
+    # include/hg_hydro.h
+    "hg_hydro_init": (_I, [_P(_V), _I, _I, _I, _D, _D, _D, _D, _I, _V]),
+    "hg_hydro_set_primitive": (_I, [_V, _V, _I, _I]),
+    "hg_hydro_set_state": (_I, [_V, _V, _I, _I]),
+    "hg_hydro_get_state": (_I, [_V, _V, _I, _I]),
+    "hg_hydro_max_speed": (_I, [_V, _P(_D)]),
+    "hg_hydro_step": (_I, [_V, _V, _D, _I]),
+    "hg_hydro_virial": (_I, [_V, _V, _P(_D)]),
+    "hg_hydro_launches": (_I, [_V, _P(ctypes.c_longlong)]),
+    "hg_hydro_free": (None, [_V]),
 }
 
 _lib = None

@@ -21,6 +21,9 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # host code: no floating-point contraction (the Robin and multipole set-up must round the same on x86 and Arm)
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2", "-Xcompiler", "-ffp-contract=off",
          "--expt-relaxed-constexpr"]
+# per-file device flags: the hydrodynamics is compiled without multiply-add contraction, so that its FP64 instance
+# rounds every operation as written (the operation order its ABI header fixes)
+FILE_FLAGS = {"hydro.cu": ["-fmad=false"]}
 
 
 def _nvcc() -> str:
@@ -49,7 +52,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         if not force and os.path.exists(obj) and os.path.getmtime(obj) >= max(os.path.getmtime(src), hdr_time):
             return obj
         tmp = f"{obj}.tmp{os.getpid()}"
-        cmd = [nvcc, *ARCH, *FLAGS, "-I", INCLUDE, "-c", src, "-o", tmp]
+        cmd = [nvcc, *ARCH, *FLAGS, *FILE_FLAGS.get(os.path.basename(src), []), "-I", INCLUDE, "-c", src, "-o", tmp]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed on {os.path.basename(src)}:\n{r.stderr}")

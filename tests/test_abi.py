@@ -59,3 +59,17 @@ def test_invalid_arguments_rejected_on_host(lib_path):
     assert b"unstable" in L.hg_last_error()
     assert L.hg_step(None, 1) == _lib.HG_ERR_ARG
     L.hg_free(None)
+
+
+def test_hydro_invalid_arguments_rejected_on_host(lib_path):
+    from paper_1602_05700_gb300 import _lib
+    L = _lib.lib()
+    h = ctypes.c_void_p()
+    assert L.hg_hydro_init(ctypes.byref(h), 0, 8, 8, 0.1, 5.0 / 3.0, 0.0, 0.0, 0, None) == _lib.HG_ERR_ARG
+    assert h.value is None
+    assert L.hg_hydro_init(ctypes.byref(h), 8, 8, 8, 0.1, 1.0, 0.0, 0.0, 0, None) == _lib.HG_ERR_ARG
+    assert L.hg_hydro_init(ctypes.byref(h), 8, 8, 8, -0.1, 5.0 / 3.0, 0.0, 0.0, 0, None) == _lib.HG_ERR_ARG
+    assert L.hg_hydro_init(ctypes.byref(h), 8, 8, 8, 0.1, 5.0 / 3.0, -1.0, 0.0, 0, None) == _lib.HG_ERR_ARG
+    assert L.hg_hydro_init(ctypes.byref(h), 8, 8, 8, 0.1, 5.0 / 3.0, 0.0, 0.0, 5, None) == _lib.HG_ERR_ARG
+    assert L.hg_hydro_step(None, None, 0.1, 1) == _lib.HG_ERR_ARG
+    assert L.hg_hydro_virial(None, None, None) == _lib.HG_ERR_ARG
