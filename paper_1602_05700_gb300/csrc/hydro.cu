@@ -1,19 +1,11 @@
-// Ideal-gas hydrodynamics that consumes the hyperbolic self-gravity (arXiv 1602.05700, Sec. 2): finite volume,
-// minmod-limited piecewise-linear primitives, HLLC fluxes with Davis' wave-speed bounds, outgoing (zero-gradient)
-// boundaries, two-stage SSP Runge-Kutta with the gravity source (0, rho a, m . a), and the virial measure of the
-// paper's Eq. VC.  The ABI is include/hg_hydro.h.
+// Ideal-gas hydrodynamics that consumes the hyperbolic self-gravity (arXiv 1602.05700, Sec. 2): the C ABI of
+// include/hg_hydro.h, the FP64 stage kernel, the set-up conversion and the FP64 reductions (characteristic speed,
+// the virial sums of the paper's Eq. VC).  The stage kernel itself is in hydro_kernels.cuh.
 //
 // This file is compiled without floating-point contraction (-fmad=false, set by the builder): the FP64 instance
-// then rounds every operation exactly as written, and the operation order below is the one the ABI header fixes,
-// so double-precision states reproduce a plain sequential evaluation of the same formulas bit for bit.
-//
-// Kernel design (one launch per Runge-Kutta stage): a block owns a 32 x 8 column of cells and marches along z
-// through a chunk of planes.  A ring of four primitive planes (the column plus a 2-cell halo in x and y) sits in
-// shared memory; each plane of the global state is read once per block and converted to primitives once.  Every
-// face flux is evaluated once: the 33 x 8 x-faces and 32 x 9 y-faces of the current plane go to shared memory,
-// the z-face above each cell is kept in registers and becomes the next plane's lower face.  The update, the
-// gravity source, the stage combination and the floors are fused into the same pass, so a stage reads the stage
-// state (and, for stage 2, the step's initial state and a) once and writes the new state once.
+// then rounds every operation exactly as written, and the operation order is the one the ABI header fixes, so
+// double-precision states reproduce a plain sequential evaluation of the same formulas bit for bit.  The FP32
+// stage kernel is instantiated in hydro_f32.cu with contraction on.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdio.h>
@@ -22,6 +14,7 @@
 
 #include "hg_hydro.h"
 #include "hg_internal.cuh"
+#include "hydro_kernels.cuh"
 
 struct hg_hydro {
     int nx, ny, nz;
@@ -43,261 +36,7 @@ namespace {
 
 using hg::fail;
 
-constexpr int TX = 32, TY = 8, NT = TX * TY, HALO = 2;
-constexpr int PX = TX + 2 * HALO, PY = TY + 2 * HALO, PCELLS = PX * PY;  // 36 x 12 cells per staged plane
-constexpr int NXF = (TX + 1) * TY;  // x-faces of one plane of the column
-constexpr int NYF = TX * (TY + 1);  // y-faces
-constexpr int kVirialSums = 5;      // sum rho phi, sum e_int, sum e_kin, sum rho (bound cells), max rho
-
-template <typename T>
-struct Smem {
-    T w[4][5][PCELLS];  // primitive planes k-1 .. k+2 (ring by plane index mod 4)
-    T fx[5][NXF];
-    T fy[5][NYF];
-};
-
-template <typename T>
-struct Gas {
-    T gamma, gm1, rho_floor, p_floor;
-};
-
-template <typename T>
-struct StageArgs {
-    const T* __restrict__ Uin;  // stage state
-    const T* U0;                // the step's initial state (stage 2; may be Uout: each cell is read, then written,
-                                // by the same thread, so neither pointer is restrict nor read through the nc path)
-    const T* __restrict__ A;    // acceleration (3 planes) or null
-    T* Uout;
-    long long n;
-    int nx, ny, nz, zb;
-    T dt, inv_h;
-    Gas<T> gas;
-};
-
-__device__ __forceinline__ int slot(int p) { return (p + 4) & 3; }  // p >= -2
-
-template <typename T>
-__device__ __forceinline__ T kinetic(const T u[5], T& vx, T& vy, T& vz) {
-    vx = u[1] / u[0];
-    vy = u[2] / u[0];
-    vz = u[3] / u[0];
-    return T(0.5) * ((u[1] * vx + u[2] * vy) + u[3] * vz);
-}
-
-template <typename T>
-__device__ __forceinline__ void cons_to_prim(T gm1, const T u[5], T w[5]) {
-    T vx, vy, vz;
-    const T ke = kinetic(u, vx, vy, vz);
-    w[0] = u[0];
-    w[1] = vx;
-    w[2] = vy;
-    w[3] = vz;
-    w[4] = gm1 * (u[4] - ke);
-}
-
-template <typename T>
-__device__ __forceinline__ void prim_to_cons(T gm1, const T w[5], T u[5]) {
-    u[0] = w[0];
-    u[1] = w[0] * w[1];
-    u[2] = w[0] * w[2];
-    u[3] = w[0] * w[3];
-    u[4] = w[4] / gm1 + T(0.5) * w[0] * ((w[1] * w[1] + w[2] * w[2]) + w[3] * w[3]);
-}
-
-template <typename T>
-__device__ __forceinline__ T minmod(T a, T b) {
-    if (a > T(0) && b > T(0)) return a < b ? a : b;
-    if (a < T(0) && b < T(0)) return a > b ? a : b;
-    return T(0);
-}
-
-// conserved state u and physical flux f along axis D of the primitive state w
-template <typename T, int D>
-__device__ __forceinline__ void state_flux(T gm1, const T w[5], T u[5], T f[5]) {
-    prim_to_cons(gm1, w, u);
-    const T un = w[1 + D];
-    const T mf = w[0] * un;
-    f[0] = mf;
-    f[1] = mf * w[1];
-    f[2] = mf * w[2];
-    f[3] = mf * w[3];
-    f[1 + D] = f[1 + D] + w[4];
-    f[4] = (u[4] + w[4]) * un;
-}
-
-// HLLC flux along axis D between primitive states wl and wr (Davis bounds, Toro-Spruce-Speares star states)
-template <typename T, int D>
-__device__ __forceinline__ void hllc(const Gas<T>& G, const T wl[5], const T wr[5], T F[5]) {
-    T ul[5], fl[5], ur[5], fr[5];
-    state_flux<T, D>(G.gm1, wl, ul, fl);
-    state_flux<T, D>(G.gm1, wr, ur, fr);
-    const T al = sqrt(G.gamma * wl[4] / wl[0]);
-    const T ar = sqrt(G.gamma * wr[4] / wr[0]);
-    const T unl = wl[1 + D], unr = wr[1 + D];
-    const T a1 = unl - al, a2 = unr - ar, b1 = unl + al, b2 = unr + ar;
-    const T sl = a1 < a2 ? a1 : a2;
-    const T sr = b1 > b2 ? b1 : b2;
-    if (sl >= T(0)) {
-#pragma unroll
-        for (int q = 0; q < 5; ++q) F[q] = fl[q];
-        return;
-    }
-    if (sr <= T(0)) {
-#pragma unroll
-        for (int q = 0; q < 5; ++q) F[q] = fr[q];
-        return;
-    }
-    const T dl = wl[0] * (sl - unl);
-    const T dr = wr[0] * (sr - unr);
-    const T ss = ((wr[4] - wl[4]) + (unl * dl - unr * dr)) / (dl - dr);
-    const bool left = ss >= T(0);
-    T w[5], u[5], f[5];
-#pragma unroll
-    for (int q = 0; q < 5; ++q) {
-        w[q] = left ? wl[q] : wr[q];
-        u[q] = left ? ul[q] : ur[q];
-        f[q] = left ? fl[q] : fr[q];
-    }
-    const T sk = left ? sl : sr;
-    const T dk = left ? dl : dr;
-    const T fac = dk / (sk - ss);
-    T us[5];
-    us[0] = fac;
-    us[1] = fac * w[1];
-    us[2] = fac * w[2];
-    us[3] = fac * w[3];
-    us[1 + D] = fac * ss;
-    us[4] = fac * (u[4] / w[0] + (ss - w[1 + D]) * (ss + w[4] / dk));
-#pragma unroll
-    for (int q = 0; q < 5; ++q) F[q] = f[q] + sk * (us[q] - u[q]);
-}
-
-// flux through the face between cells c1 and c2 of the four consecutive staged cells c0..c3 (component stride
-// PCELLS): minmod-limited left and right states, then HLLC along axis D
-template <typename T, int D>
-__device__ __forceinline__ void flux4(const Gas<T>& G, const T* c0, const T* c1, const T* c2, const T* c3, T F[5]) {
-    T wl[5], wr[5];
-#pragma unroll
-    for (int q = 0; q < 5; ++q) {
-        const T a = c0[q * PCELLS], b = c1[q * PCELLS], c = c2[q * PCELLS], d = c3[q * PCELLS];
-        wl[q] = b + T(0.5) * minmod(b - a, c - b);
-        wr[q] = c - T(0.5) * minmod(c - b, d - c);
-    }
-    hllc<T, D>(G, wl, wr, F);
-}
-
-// stage plane p (clamped into the grid: the outgoing boundary's zero-gradient ghosts) of the column at (i0, j0)
-template <typename T>
-__device__ __forceinline__ void stage_plane(T (*ws)[PCELLS], const StageArgs<T>& a, int i0, int j0, int p) {
-    const int kk = min(max(p, 0), a.nz - 1);
-    for (int c = threadIdx.x; c < PCELLS; c += NT) {
-        const int lx = c % PX, ly = c / PX;
-        const int i = min(max(i0 - HALO + lx, 0), a.nx - 1);
-        const int j = min(max(j0 - HALO + ly, 0), a.ny - 1);
-        const long long o = ((long long)kk * a.ny + j) * a.nx + i;
-        T u[5], w[5];
-#pragma unroll
-        for (int q = 0; q < 5; ++q) u[q] = __ldg(a.Uin + q * a.n + o);
-        cons_to_prim(a.gas.gm1, u, w);
-#pragma unroll
-        for (int q = 0; q < 5; ++q) ws[q][c] = w[q];
-    }
-}
-
-template <typename T>
-__device__ __forceinline__ void apply_floors(const Gas<T>& G, T u[5]) {
-    if (u[0] < G.rho_floor) u[0] = G.rho_floor;
-    T vx, vy, vz;
-    const T ke = kinetic(u, vx, vy, vz);
-    const T p = G.gm1 * (u[4] - ke);
-    if (p < G.p_floor) u[4] = G.p_floor / G.gm1 + ke;
-}
-
-// One Runge-Kutta stage: STAGE 1 writes u0 + dt L(u0); STAGE 2 writes (u0 + (u1 + dt L(u1))) / 2.
-template <typename T, int STAGE>
-__global__ void __launch_bounds__(NT, sizeof(T) == 8 ? 2 : 3) k_hydro_stage(StageArgs<T> a) {
-    extern __shared__ __align__(16) unsigned char smraw[];
-    Smem<T>& sm = *reinterpret_cast<Smem<T>*>(smraw);
-    const int tid = threadIdx.x, tx = tid & (TX - 1), ty = tid / TX;
-    const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
-    const int k0 = blockIdx.z * a.zb, k1 = min(a.nz, k0 + a.zb);
-    const int i = i0 + tx, j = j0 + ty;
-    const bool own = i < a.nx && j < a.ny;
-    const int cc = (ty + HALO) * PX + tx + HALO;  // this thread's cell in a staged plane
-    const Gas<T> G = a.gas;
-
-    for (int p = k0 - 2; p <= k0 + 1; ++p) stage_plane(sm.w[slot(p)], a, i0, j0, p);
-    __syncthreads();
-    T fzl[5], fzh[5];
-    flux4<T, 2>(G, &sm.w[slot(k0 - 2)][0][cc], &sm.w[slot(k0 - 1)][0][cc], &sm.w[slot(k0)][0][cc],
-                &sm.w[slot(k0 + 1)][0][cc], fzl);
-    __syncthreads();  // plane k0-2's slot is refilled next
-
-    for (int k = k0; k < k1; ++k) {
-        T u[5], u0[5], acc[3];
-        const long long o = ((long long)k * a.ny + (own ? j : 0)) * a.nx + (own ? i : 0);
-        if (own) {
-#pragma unroll
-            for (int q = 0; q < 5; ++q) u[q] = __ldg(a.Uin + q * a.n + o);
-            if (STAGE == 2) {
-#pragma unroll
-                for (int q = 0; q < 5; ++q) u0[q] = a.U0[q * a.n + o];
-            }
-            if (a.A) {
-#pragma unroll
-                for (int q = 0; q < 3; ++q) acc[q] = __ldg(a.A + q * a.n + o);
-            }
-        }
-        stage_plane(sm.w[slot(k + 2)], a, i0, j0, k + 2);
-        __syncthreads();
-        const T(*W)[PCELLS] = sm.w[slot(k)];
-        for (int f = tid; f < NXF; f += NT) {
-            const int row = f / (TX + 1), af = f - row * (TX + 1);
-            const int c0 = (row + HALO) * PX + af;  // cells af-2 .. af+1 of the row: the face between af-1 and af
-            T F[5];
-            flux4<T, 0>(G, &W[0][c0], &W[0][c0 + 1], &W[0][c0 + 2], &W[0][c0 + 3], F);
-#pragma unroll
-            for (int q = 0; q < 5; ++q) sm.fx[q][f] = F[q];
-        }
-        for (int f = tid; f < NYF; f += NT) {
-            const int fj = f / TX, col = f - fj * TX;
-            const int c0 = fj * PX + col + HALO;  // rows fj-2 .. fj+1 of the column: the face between fj-1 and fj
-            T F[5];
-            flux4<T, 1>(G, &W[0][c0], &W[0][c0 + PX], &W[0][c0 + 2 * PX], &W[0][c0 + 3 * PX], F);
-#pragma unroll
-            for (int q = 0; q < 5; ++q) sm.fy[q][f] = F[q];
-        }
-        flux4<T, 2>(G, &sm.w[slot(k - 1)][0][cc], &sm.w[slot(k)][0][cc], &sm.w[slot(k + 1)][0][cc],
-                    &sm.w[slot(k + 2)][0][cc], fzh);
-        __syncthreads();
-        if (own) {
-            T r[5], un[5];
-#pragma unroll
-            for (int q = 0; q < 5; ++q) {
-                r[q] = sm.fx[q][ty * (TX + 1) + tx] - sm.fx[q][ty * (TX + 1) + tx + 1];
-                r[q] = r[q] + (sm.fy[q][ty * TX + tx] - sm.fy[q][(ty + 1) * TX + tx]);
-                r[q] = r[q] + (fzl[q] - fzh[q]);
-                r[q] = r[q] * a.inv_h;
-            }
-            if (a.A) {
-                r[1] = r[1] + u[0] * acc[0];
-                r[2] = r[2] + u[0] * acc[1];
-                r[3] = r[3] + u[0] * acc[2];
-                r[4] = r[4] + ((u[1] * acc[0] + u[2] * acc[1]) + u[3] * acc[2]);
-            }
-#pragma unroll
-            for (int q = 0; q < 5; ++q) {
-                if (STAGE == 1) un[q] = u[q] + a.dt * r[q];
-                else un[q] = T(0.5) * (u0[q] + (u[q] + a.dt * r[q]));
-            }
-            apply_floors(G, un);
-#pragma unroll
-            for (int q = 0; q < 5; ++q) a.Uout[q * a.n + o] = un[q];
-        }
-#pragma unroll
-        for (int q = 0; q < 5; ++q) fzl[q] = fzh[q];
-    }
-}
+constexpr int kVirialSums = 5;  // sum rho phi, sum e_int, sum e_kin, sum rho (bound cells), max rho
 
 template <typename Tin, typename T>
 __global__ void k_prim_to_cons(const Tin* __restrict__ W, T* __restrict__ U, long long n, T gm1) {
@@ -402,42 +141,28 @@ int stage_zb(const hg_hydro* H) {
     return (int)zb;
 }
 
-template <typename T>
-int launch_stage(hg_hydro* H, int stage, const void* Uin, const void* U0, const void* A, void* Uout, double dt) {
-    static unsigned long long attr_done[2] = {0, 0};
-    StageArgs<T> a;
-    a.Uin = (const T*)Uin;
-    a.U0 = (const T*)U0;
-    a.A = (const T*)A;
-    a.Uout = (T*)Uout;
-    a.n = H->n;
-    a.nx = H->nx;
-    a.ny = H->ny;
-    a.nz = H->nz;
-    a.zb = stage_zb(H);
-    a.dt = (T)dt;
-    a.inv_h = (T)(1.0 / H->h);
-    a.gas.gamma = (T)H->gamma;
-    a.gas.gm1 = (T)(H->gamma - 1.0);
-    a.gas.rho_floor = (T)H->rho_floor;
-    a.gas.p_floor = (T)H->p_floor;
-    const int smem = (int)sizeof(Smem<T>);
-    dim3 grid((H->nx + TX - 1) / TX, (H->ny + TY - 1) / TY, (H->nz + a.zb - 1) / a.zb);
-    int rc;
-    if (stage == 1) {
-        if ((rc = hg::smem_attr_once((const void*)k_hydro_stage<T, 1>, smem, &attr_done[0]))) return rc;
-        k_hydro_stage<T, 1><<<grid, NT, smem, H->stream>>>(a);
-    } else {
-        if ((rc = hg::smem_attr_once((const void*)k_hydro_stage<T, 2>, smem, &attr_done[1]))) return rc;
-        k_hydro_stage<T, 2><<<grid, NT, smem, H->stream>>>(a);
-    }
-    HH_LAUNCHED("k_hydro_stage");
-    return HG_OK;
-}
-
 int launch_stage_any(hg_hydro* H, int stage, const void* Uin, const void* U0, const void* A, void* Uout, double dt) {
-    return H->dtype == HG_DT_F64 ? launch_stage<double>(H, stage, Uin, U0, A, Uout, dt)
-                                 : launch_stage<float>(H, stage, Uin, U0, A, Uout, dt);
+    hg::HydroStageLaunch L;
+    L.stream = H->stream;
+    L.nx = H->nx;
+    L.ny = H->ny;
+    L.nz = H->nz;
+    L.zb = stage_zb(H);
+    L.stage = stage;
+    L.n = H->n;
+    L.h = H->h;
+    L.gamma = H->gamma;
+    L.rho_floor = H->rho_floor;
+    L.p_floor = H->p_floor;
+    L.dt = dt;
+    L.Uin = Uin;
+    L.U0 = U0;
+    L.A = A;
+    L.Uout = Uout;
+    const cudaError_t e = H->dtype == HG_DT_F64 ? hg::hydro_stage_f64(L) : hg::hydro_stage_f32(L);
+    ++H->launches;
+    if (e != cudaSuccess) return hg::cuda_fail(e, "k_hydro_stage");
+    return HG_OK;
 }
 
 int prim_to_cons_launch(hg_hydro* H, const void* W, int dtype) {
@@ -471,6 +196,10 @@ void release(hg_hydro* H) {
 }
 
 }  // namespace
+
+namespace hg {
+cudaError_t hydro_stage_f64(const HydroStageLaunch& L) { return launch_hydro_stage<double>(L); }
+}  // namespace hg
 
 extern "C" {
 
