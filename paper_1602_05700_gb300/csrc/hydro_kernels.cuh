@@ -8,7 +8,7 @@
 // Runge-Kutta with the gravity source (0, rho a, m . a), floors after each stage.
 //
 // Kernel design (one launch per Runge-Kutta stage): a block owns a 32 x 8 column of cells and marches along z
-// through a chunk of planes.  A ring of four primitive planes (the column plus a 2-cell halo in x and y) sits in
+// through a chunk of planes.  A ring of primitive planes (the column plus a 2-cell halo in x and y) sits in
 // shared memory; each plane of the global state is read once per block and converted to primitives once.  Every
 // face flux is evaluated once: the 33 x 8 x-faces and 32 x 9 y-faces of the current plane form one pool of work
 // over the block's threads and go to shared memory; the z-face above each cell is kept in registers and becomes
@@ -55,11 +55,22 @@ __device__ __forceinline__ float hsqrt(float x) {
     return r;
 }
 
+// Shared-memory ring of staged planes.  FP32: five planes and double-buffered face fluxes, so one barrier per plane
+// suffices (plane k+2 is staged and the x/y-faces of plane k computed before it; the z-face and the update after
+// it).  FP64: four planes and one face buffer (the smaller footprint keeps two blocks per SM), two barriers per plane.
+template <typename T>
+struct Ring {
+    static constexpr int planes = sizeof(T) == 4 ? 5 : 4;
+    static constexpr int bufs = planes == 5 ? 2 : 1;
+    static constexpr bool one_barrier = planes == 5;
+    __device__ static __forceinline__ int slot(int p) { return (p + 2 * planes) % planes; }  // p >= -2
+};
+
 template <typename T>
 struct Smem {
-    T w[4][5][PCELLS];  // primitive planes k-1 .. k+2 (ring by plane index mod 4)
-    T fx[5][NXF];
-    T fy[5][NYF];
+    T w[Ring<T>::planes][5][PCELLS];  // primitive planes, ring by plane index
+    T fx[Ring<T>::bufs][5][NXF];
+    T fy[Ring<T>::bufs][5][NYF];
 };
 
 template <typename T>
@@ -80,7 +91,6 @@ struct StageArgs {
     Gas<T> gas;
 };
 
-__device__ __forceinline__ int slot(int p) { return (p + 4) & 3; }  // p >= -2
 
 template <typename T>
 __device__ __forceinline__ T kinetic(const T u[5], T& vx, T& vy, T& vz) {
@@ -110,11 +120,16 @@ __device__ __forceinline__ void prim_to_cons(T gm1, const T w[5], T u[5]) {
     u[4] = hdiv(w[4], gm1) + T(0.5) * w[0] * ((w[1] * w[1] + w[2] * w[2]) + w[3] * w[3]);
 }
 
-template <typename T>
-__device__ __forceinline__ T minmod(T a, T b) {
-    if (a > T(0) && b > T(0)) return a < b ? a : b;
-    if (a < T(0) && b < T(0)) return a > b ? a : b;
-    return T(0);
+// minmod: the smaller slope in magnitude when both have the same sign, else 0.  FP64 in the comparison form the
+// ABI header states; FP32 branch-free (the same value up to the sign of a zero result, which no later operation can
+// distinguish except through another zero)
+__device__ __forceinline__ double minmod(double a, double b) {
+    if (a > 0.0 && b > 0.0) return a < b ? a : b;
+    if (a < 0.0 && b < 0.0) return a > b ? a : b;
+    return 0.0;
+}
+__device__ __forceinline__ float minmod(float a, float b) {
+    return 0.5f * (copysignf(1.0f, a) + copysignf(1.0f, b)) * fminf(fabsf(a), fabsf(b));
 }
 
 // conserved state u and physical flux f along axis D of the primitive state w
@@ -143,15 +158,18 @@ __device__ __forceinline__ void hllc(const Gas<T>& G, const T wl[5], const T wr[
     const T a1 = unl - al, a2 = unr - ar, b1 = unl + al, b2 = unr + ar;
     const T sl = a1 < a2 ? a1 : a2;
     const T sr = b1 > b2 ? b1 : b2;
-    if (sl >= T(0)) {
+    constexpr bool kSelect = sizeof(T) == 4;  // FP32: evaluate the star state always and select (no divergence)
+    if (!kSelect) {
+        if (sl >= T(0)) {
 #pragma unroll
-        for (int q = 0; q < 5; ++q) F[q] = fl[q];
-        return;
-    }
-    if (sr <= T(0)) {
+            for (int q = 0; q < 5; ++q) F[q] = fl[q];
+            return;
+        }
+        if (sr <= T(0)) {
 #pragma unroll
-        for (int q = 0; q < 5; ++q) F[q] = fr[q];
-        return;
+            for (int q = 0; q < 5; ++q) F[q] = fr[q];
+            return;
+        }
     }
     const T dl = wl[0] * (sl - unl);
     const T dr = wr[0] * (sr - unr);
@@ -176,6 +194,10 @@ __device__ __forceinline__ void hllc(const Gas<T>& G, const T wl[5], const T wr[
     us[4] = fac * (hdiv(u[4], w[0]) + (ss - w[1 + D]) * (ss + hdiv(w[4], dk)));
 #pragma unroll
     for (int q = 0; q < 5; ++q) F[q] = f[q] + sk * (us[q] - u[q]);
+    if (kSelect) {  // supersonic faces take the upwind state's flux (a non-finite star value is never selected)
+#pragma unroll
+        for (int q = 0; q < 5; ++q) F[q] = sl >= T(0) ? fl[q] : (sr <= T(0) ? fr[q] : F[q]);
+    }
 }
 
 // flux through the face between cells c1 and c2 of the four consecutive staged cells c0..c3 (component stride
@@ -231,13 +253,14 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 8 ? 2 : 3) k_hydro_stage(Stag
     const bool own = i < a.nx && j < a.ny;
     const int cc = (ty + HALO) * PX + tx + HALO;  // this thread's cell in a staged plane
     const Gas<T> G = a.gas;
+    using R = Ring<T>;
 
-    for (int p = k0 - 2; p <= k0 + 1; ++p) stage_plane(sm.w[slot(p)], a, i0, j0, p);
+    for (int p = k0 - 2; p <= k0 + 1; ++p) stage_plane(sm.w[R::slot(p)], a, i0, j0, p);
     __syncthreads();
     T fzl[5], fzh[5];
-    flux4<T, 2>(G, &sm.w[slot(k0 - 2)][0][cc], &sm.w[slot(k0 - 1)][0][cc], &sm.w[slot(k0)][0][cc],
-                &sm.w[slot(k0 + 1)][0][cc], fzl);
-    __syncthreads();  // plane k0-2's slot is refilled next
+    flux4<T, 2>(G, &sm.w[R::slot(k0 - 2)][0][cc], &sm.w[R::slot(k0 - 1)][0][cc], &sm.w[R::slot(k0)][0][cc],
+                &sm.w[R::slot(k0 + 1)][0][cc], fzl);
+    if (!R::one_barrier) __syncthreads();  // with four slots, plane k0-2's slot is refilled next
 
     for (int k = k0; k < k1; ++k) {
         T u[5], u0[5], acc[3];
@@ -254,9 +277,10 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 8 ? 2 : 3) k_hydro_stage(Stag
                 for (int q = 0; q < 3; ++q) acc[q] = __ldg(a.A + q * a.n + o);
             }
         }
-        stage_plane(sm.w[slot(k + 2)], a, i0, j0, k + 2);
-        __syncthreads();
-        const T(*W)[PCELLS] = sm.w[slot(k)];
+        stage_plane(sm.w[R::slot(k + 2)], a, i0, j0, k + 2);
+        if (!R::one_barrier) __syncthreads();
+        const int b = R::one_barrier ? (k & 1) : 0;
+        const T(*W)[PCELLS] = sm.w[R::slot(k)];
         // x- and y-faces of plane k as one pool of NXF + NYF fluxes
         for (int f = tid; f < NXF + NYF; f += NT) {
             T F[5];
@@ -265,25 +289,29 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 8 ? 2 : 3) k_hydro_stage(Stag
                 const int c0 = (row + HALO) * PX + af;  // cells af-2 .. af+1 of the row: the face between af-1, af
                 flux4<T, 0>(G, &W[0][c0], &W[0][c0 + 1], &W[0][c0 + 2], &W[0][c0 + 3], F);
 #pragma unroll
-                for (int q = 0; q < 5; ++q) sm.fx[q][f] = F[q];
+                for (int q = 0; q < 5; ++q) sm.fx[b][q][f] = F[q];
             } else {
                 const int g = f - NXF;
                 const int fj = g / TX, col = g - fj * TX;
                 const int c0 = fj * PX + col + HALO;  // rows fj-2 .. fj+1 of the column: the face between fj-1, fj
                 flux4<T, 1>(G, &W[0][c0], &W[0][c0 + PX], &W[0][c0 + 2 * PX], &W[0][c0 + 3 * PX], F);
 #pragma unroll
-                for (int q = 0; q < 5; ++q) sm.fy[q][g] = F[q];
+                for (int q = 0; q < 5; ++q) sm.fy[b][q][g] = F[q];
             }
         }
-        flux4<T, 2>(G, &sm.w[slot(k - 1)][0][cc], &sm.w[slot(k)][0][cc], &sm.w[slot(k + 1)][0][cc],
-                    &sm.w[slot(k + 2)][0][cc], fzh);
+        if (!R::one_barrier)
+            flux4<T, 2>(G, &sm.w[R::slot(k - 1)][0][cc], &sm.w[R::slot(k)][0][cc], &sm.w[R::slot(k + 1)][0][cc],
+                        &sm.w[R::slot(k + 2)][0][cc], fzh);
         __syncthreads();
+        if (R::one_barrier)
+            flux4<T, 2>(G, &sm.w[R::slot(k - 1)][0][cc], &sm.w[R::slot(k)][0][cc], &sm.w[R::slot(k + 1)][0][cc],
+                        &sm.w[R::slot(k + 2)][0][cc], fzh);
         if (own) {
             T r[5], un[5];
 #pragma unroll
             for (int q = 0; q < 5; ++q) {
-                r[q] = sm.fx[q][ty * (TX + 1) + tx] - sm.fx[q][ty * (TX + 1) + tx + 1];
-                r[q] = r[q] + (sm.fy[q][ty * TX + tx] - sm.fy[q][(ty + 1) * TX + tx]);
+                r[q] = sm.fx[b][q][ty * (TX + 1) + tx] - sm.fx[b][q][ty * (TX + 1) + tx + 1];
+                r[q] = r[q] + (sm.fy[b][q][ty * TX + tx] - sm.fy[b][q][(ty + 1) * TX + tx]);
                 r[q] = r[q] + (fzl[q] - fzh[q]);
                 r[q] = r[q] * a.inv_h;
             }
