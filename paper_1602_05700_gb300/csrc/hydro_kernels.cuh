@@ -121,15 +121,15 @@ __device__ __forceinline__ void prim_to_cons(T gm1, const T w[5], T u[5]) {
 }
 
 // minmod: the smaller slope in magnitude when both have the same sign, else 0.  FP64 in the comparison form the
-// ABI header states; FP32 branch-free (the same value up to the sign of a zero result, which no later operation can
-// distinguish except through another zero)
+// ABI header states; FP32 branch-free as the median of (a, b, 0) (the same value up to the sign of a zero result,
+// which no later operation can distinguish except through another zero)
 __device__ __forceinline__ double minmod(double a, double b) {
     if (a > 0.0 && b > 0.0) return a < b ? a : b;
     if (a < 0.0 && b < 0.0) return a > b ? a : b;
     return 0.0;
 }
 __device__ __forceinline__ float minmod(float a, float b) {
-    return 0.5f * (copysignf(1.0f, a) + copysignf(1.0f, b)) * fminf(fabsf(a), fabsf(b));
+    return fmaxf(fminf(a, b), fminf(fmaxf(a, b), 0.0f));  // the median of (a, b, 0)
 }
 
 // conserved state u and physical flux f along axis D of the primitive state w
@@ -146,44 +146,30 @@ __device__ __forceinline__ void state_flux(T gm1, const T w[5], T u[5], T f[5]) 
     f[4] = (u[4] + w[4]) * un;
 }
 
-// HLLC flux along axis D between primitive states wl and wr (Davis bounds, Toro-Spruce-Speares star states)
+// HLLC flux along axis D between primitive states wl and wr (Davis bounds, Toro-Spruce-Speares star states).
+// Only the side the flux is taken from is converted to a conserved state and a physical flux: the left one if
+// S_L >= 0, the right one if S_R <= 0 (supersonic: that side's physical flux), else the side of the contact speed's
+// sign (F = F_K + S_K (U*_K - U_K)).  Every value is computed by the same operations as a version that evaluates
+// both sides and then picks one.
 template <typename T, int D>
 __device__ __forceinline__ void hllc(const Gas<T>& G, const T wl[5], const T wr[5], T F[5]) {
-    T ul[5], fl[5], ur[5], fr[5];
-    state_flux<T, D>(G.gm1, wl, ul, fl);
-    state_flux<T, D>(G.gm1, wr, ur, fr);
     const T al = hsqrt(hdiv(G.gamma * wl[4], wl[0]));
     const T ar = hsqrt(hdiv(G.gamma * wr[4], wr[0]));
     const T unl = wl[1 + D], unr = wr[1 + D];
     const T a1 = unl - al, a2 = unr - ar, b1 = unl + al, b2 = unr + ar;
     const T sl = a1 < a2 ? a1 : a2;
     const T sr = b1 > b2 ? b1 : b2;
-    constexpr bool kSelect = sizeof(T) == 4;  // FP32: evaluate the star state always and select (no divergence)
-    if (!kSelect) {
-        if (sl >= T(0)) {
-#pragma unroll
-            for (int q = 0; q < 5; ++q) F[q] = fl[q];
-            return;
-        }
-        if (sr <= T(0)) {
-#pragma unroll
-            for (int q = 0; q < 5; ++q) F[q] = fr[q];
-            return;
-        }
-    }
     const T dl = wl[0] * (sl - unl);
     const T dr = wr[0] * (sr - unr);
     const T ss = hdiv((wr[4] - wl[4]) + (unl * dl - unr * dr), dl - dr);
-    const bool left = ss >= T(0);
+    const bool upwind = sl >= T(0) || sr <= T(0);
+    const bool left = sl >= T(0) || (sr > T(0) && ss >= T(0));
     T w[5], u[5], f[5];
 #pragma unroll
-    for (int q = 0; q < 5; ++q) {
-        w[q] = left ? wl[q] : wr[q];
-        u[q] = left ? ul[q] : ur[q];
-        f[q] = left ? fl[q] : fr[q];
-    }
+    for (int q = 0; q < 5; ++q) w[q] = left ? wl[q] : wr[q];
     const T sk = left ? sl : sr;
     const T dk = left ? dl : dr;
+    state_flux<T, D>(G.gm1, w, u, f);
     const T fac = hdiv(dk, sk - ss);
     T us[5];
     us[0] = fac;
@@ -193,12 +179,8 @@ __device__ __forceinline__ void hllc(const Gas<T>& G, const T wl[5], const T wr[
     us[1 + D] = fac * ss;
     us[4] = fac * (hdiv(u[4], w[0]) + (ss - w[1 + D]) * (ss + hdiv(w[4], dk)));
 #pragma unroll
-    for (int q = 0; q < 5; ++q) F[q] = f[q] + sk * (us[q] - u[q]);
-    if (kSelect) {  // supersonic faces take the upwind state's flux (a non-finite star value is never selected)
-#pragma unroll
-        for (int q = 0; q < 5; ++q) F[q] = sl >= T(0) ? fl[q] : (sr <= T(0) ? fr[q] : F[q]);
-    }
-}
+    for (int q = 0; q < 5; ++q) F[q] = upwind ? f[q] : f[q] + sk * (us[q] - u[q]);  // a non-finite star value of a
+}                                                                                    // supersonic face is never used
 
 // flux through the face between cells c1 and c2 of the four consecutive staged cells c0..c3 (component stride
 // PCELLS): minmod-limited left and right states, then HLLC along axis D
