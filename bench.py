@@ -67,6 +67,22 @@ def source_hash(files=None):
     return h.hexdigest()
 
 
+def kernel_instructions(kernel, cells):
+    """Warp instructions per launch (scaled to `cells`) from profiles/traffic.json, if counted on the current
+    sources of that kernel."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    e = json.load(open(p)).get("kernels", {}).get(kernel)
+    if not e or "warp_inst_per_launch" not in e or e.get("sources_sha256") != source_hash(e.get("sources")):
+        return None
+    return e["warp_inst_per_launch"] * cells / e["cells"]
+
+
+# instruction-issue limit of the GPU: 152 SMs x 4 schedulers x one warp instruction per cycle at 2.07 GHz
+ISSUE_PEAK_GWIPS = 152 * 4 * 2.07
+
+
 def stencil_traffic(kernel, n):
     """DRAM bytes per launch (scaled to n^3 cells) from profiles/traffic.json, if taken on the current sources of
     that kernel (the entry lists the files it is built from and their sha256)."""
@@ -716,6 +732,7 @@ def run_virial(args):
         t, nsub, wall = 0.0, None, 0.0
         every = max(1, steps // 40)
         e0, e1 = ev(), ev()
+        H.profile(True)  # events around every stage launch of the evolution
         for it in range(steps):
             if it % 10 == 0:
                 nsub = max(1, int(np.floor(cfl * h / H.max_speed() / dtg)))
@@ -728,12 +745,15 @@ def run_virial(args):
                 wall += e0.elapsed_time(e1)
                 v = H.virial(g)
                 trace.append((round(t / t_dyn, 4), v["VC"], v["rho_max"] / v0["rho_max"]))
+        stage_ms, stage_n = H.profile_read()
+        H.profile(False)
         vc = np.array([r[1] for r in trace])
         res[label] = {"t_end_over_t_dyn": round(t / t_dyn, 3), "substeps_per_hydro_step": nsub,
                       "VC_initial": trace[0][1], "VC_final": trace[-1][1],
                       "VC_max_abs": float(np.abs(vc).max()), "VC_max_abs_after_1_t_dyn":
-                      float(max((abs(r[1]) for r in trace if r[0] >= 1.0), default=float("nan"))),
-                      "rho_max_ratio_final": trace[-1][2], "trace_t_VC_rhomax": trace[::4] + [trace[-1]]}
+                      max((abs(r[1]) for r in trace if r[0] >= 1.0), default=None),
+                      "rho_max_ratio_final": trace[-1][2], "trace_t_VC_rhomax": trace[::4] + [trace[-1]],
+                      "stage_kernel_ms_avg": round(stage_ms / max(stage_n, 1), 5), "stage_launches": stage_n}
         if label == "unperturbed":
             # time split of one coupled step: the whole step, its gravity part, and the hydro stages alone
             torch.cuda.synchronize()
@@ -751,20 +771,31 @@ def run_virial(args):
                 torch.cuda.synchronize()
                 return a.elapsed_time(b) / reps
 
+            torch.cuda.cudart().cudaProfilerStart()  # an external profiler captures just these coupled steps
             ms_step = timed(lambda: H.step(dt, g, nsub))
+            torch.cuda.cudart().cudaProfilerStop()
             rho_d = H.state()[0].contiguous()
             ms_grav = timed(lambda: (g.set_density(rho_d), g.step(nsub), g.accel()))
             ms_hyd = timed(lambda: H.step(dt))
-            alg = 50 * n ** 3  # bytes per stage launch without gravity: avg of (5 read + 5 write) and (10 + 5) floats
             pk, kind = peaks()
+            t_stage = res[label]["stage_kernel_ms_avg"] * 1e-3  # event-timed stage launches of the evolution
+            alg = 62 * n ** 3  # bytes per stage launch with gravity: avg of (8 read + 5 write) and (13 + 5) floats
+            winst = kernel_instructions("k_hydro_stage<float>", n ** 3)
             res["timing"] = {"ms_per_coupled_step": round(ms_step, 4), "ms_gravity_substeps_and_accel": round(ms_grav, 4),
-                             "ms_hydro_two_stages": round(ms_hyd, 4),
+                             "ms_hydro_two_stages_without_gravity": round(ms_hyd, 4),
                              "gcell_hydro_steps_per_s": round(n ** 3 / (ms_step * 1e-3) / 1e9, 3),
-                             "hydro_stage_roofline": {"bound": "hbm", "kernel": "k_hydro_stage<float>",
-                                                      "achieved": round(alg / (ms_hyd / 2 * 1e-3) / 1e9, 1),
-                                                      "peak": pk, "unit": "GB/s",
-                                                      "frac": round(alg / (ms_hyd / 2 * 1e-3) / 1e9 / pk, 4),
-                                                      "peak_kind": kind, "alg_bytes_per_launch": alg}}
+                             "hydro_stage_roofline": {
+                                 "bound": "alu", "kernel": "k_hydro_stage<float>", "unit": "G warp-instr/s",
+                                 "achieved": round(winst / t_stage / 1e9, 1) if winst else None,
+                                 "peak": round(ISSUE_PEAK_GWIPS, 1),
+                                 "frac": round(winst / t_stage / 1e9 / ISSUE_PEAK_GWIPS, 4) if winst else None,
+                                 "peak_kind": "instruction issue limit, 152 SMs x 4 schedulers x 2.07 GHz",
+                                 "warp_inst_per_launch": round(winst) if winst else None,
+                                 "avg_launch_ms": round(t_stage * 1e3, 5),
+                                 "hbm_achieved_gbs": round(alg / t_stage / 1e9, 1),
+                                 "hbm_frac": round(alg / t_stage / 1e9 / pk, 4), "hbm_peak_kind": kind,
+                                 "alg_bytes_per_launch": alg,
+                                 "traffic": stencil_traffic("k_hydro_stage<float>", n)}}
         g.free()
         H.free()
     return res

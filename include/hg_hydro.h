@@ -72,6 +72,12 @@ int hg_hydro_virial(hg_hydro* H, hg_grid* g, double out[6]);
 /* Kernel launches made by this hydro state so far (the coupled step's gravity launches are counted by g). */
 int hg_hydro_launches(hg_hydro* H, long long* n);
 
+/* Measurement of the Runge-Kutta stage kernel: while enabled, CUDA events on the stream bracket every stage launch.
+ * hg_hydro_profile_read synchronises the stream, returns the summed event time (ms) and the number of stage launches
+ * since the last read, and resets both.  Disabling keeps what was recorded until the next read. */
+int hg_hydro_profile(hg_hydro* H, int enable);
+int hg_hydro_profile_read(hg_hydro* H, double* stage_ms, long long* stage_launches);
+
 void hg_hydro_free(hg_hydro* H);
 
 #ifdef __cplusplus

@@ -414,6 +414,15 @@ class Hydro:
         _lib.check(_lib.lib().hg_hydro_launches(self.handle, ctypes.byref(n)))
         return n.value
 
+    def profile(self, enable=True):
+        _lib.check(_lib.lib().hg_hydro_profile(self.handle, 1 if enable else 0))
+
+    def profile_read(self):
+        """(summed stage-kernel ms, stage launches) since the last read; resets both."""
+        ms, n = ctypes.c_double(), ctypes.c_longlong()
+        _lib.check(_lib.lib().hg_hydro_profile_read(self.handle, ctypes.byref(ms), ctypes.byref(n)))
+        return ms.value, n.value
+
     def free(self):
         if getattr(self, "_h", None) is not None:
             _lib.lib().hg_hydro_free(self._h)

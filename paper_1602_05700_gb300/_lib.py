@@ -91,6 +91,8 @@ SIGNATURES = {
     "hg_hydro_step": (_I, [_V, _V, _D, _I]),
     "hg_hydro_virial": (_I, [_V, _V, _P(_D)]),
     "hg_hydro_launches": (_I, [_V, _P(ctypes.c_longlong)]),
+    "hg_hydro_profile": (_I, [_V, _I]),
+    "hg_hydro_profile_read": (_I, [_V, _P(_D), _P(ctypes.c_longlong)]),
     "hg_hydro_free": (None, [_V]),
 }
 

@@ -30,6 +30,11 @@ struct hg_hydro {
     double* red;     // reduction partials
     double* dres;    // reduction results
     long long launches;
+    // stage-kernel timing (hg_hydro_profile): event pairs around each stage launch, folded into prof_ms when read
+    int prof, prof_used;
+    double prof_ms;
+    long long prof_count;
+    cudaEvent_t* prof_ev;
 };
 
 namespace {
@@ -67,25 +72,25 @@ __global__ void __launch_bounds__(hg::kRedThreads) k_max_speed(const T* __restri
     if (threadIdx.x == 0) red[blockIdx.x] = m;
 }
 
-// per-block partial sums over the bound cells (E + rho phi < 0), in FP64 from the state's values
+// per-block partial sums over the bound cells (E + rho phi < 0), accumulated in FP64.  The kinetic energy of a cell
+// is |m|^2 / (2 rho), one division (FP64 division is a long instruction sequence on this GPU), in the state's
+// precision: the sums are compared with a sequential FP64 evaluation within a relative tolerance, not bit for bit.
 template <typename T>
 __global__ void __launch_bounds__(hg::kRedThreads) k_virial(const T* __restrict__ U, const double* __restrict__ phi,
                                                            long long n, double* __restrict__ red) {
     __shared__ double sh[32];
     double acc[kVirialSums] = {0.0, 0.0, 0.0, 0.0, 0.0};
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
-        double u[5];
-#pragma unroll
-        for (int q = 0; q < 5; ++q) u[q] = (double)U[q * n + c];
-        if (u[0] > acc[4]) acc[4] = u[0];
-        const double rp = u[0] * phi[c];
-        if (u[4] + rp < 0.0) {
-            double vx, vy, vz;
-            const double ke = kinetic(u, vx, vy, vz);
+        const T r = U[c], m1 = U[n + c], m2 = U[2 * n + c], m3 = U[3 * n + c], E = U[4 * n + c];
+        const double rd = (double)r;
+        if (rd > acc[4]) acc[4] = rd;
+        const double rp = rd * phi[c];
+        if ((double)E + rp < 0.0) {
+            const double ke = (double)(T(0.5) * hdiv((m1 * m1 + m2 * m2) + m3 * m3, r));
             acc[0] += rp;
-            acc[1] += u[4] - ke;
+            acc[1] += (double)E - ke;
             acc[2] += ke;
-            acc[3] += u[0];
+            acc[3] += rd;
         }
     }
 #pragma unroll
@@ -141,6 +146,21 @@ int stage_zb(const hg_hydro* H) {
     return (int)zb;
 }
 
+constexpr int kHydroProfPairs = 1024;
+
+int hydro_prof_fold(hg_hydro* H) {
+    if (!H->prof_used) return HG_OK;
+    HG_CUDA(cudaStreamSynchronize(H->stream));
+    for (int p = 0; p < H->prof_used; ++p) {
+        float ms = 0.f;
+        HG_CUDA(cudaEventElapsedTime(&ms, H->prof_ev[2 * p], H->prof_ev[2 * p + 1]));
+        H->prof_ms += ms;
+    }
+    H->prof_count += H->prof_used;
+    H->prof_used = 0;
+    return HG_OK;
+}
+
 int launch_stage_any(hg_hydro* H, int stage, const void* Uin, const void* U0, const void* A, void* Uout, double dt) {
     hg::HydroStageLaunch L;
     L.stream = H->stream;
@@ -159,9 +179,20 @@ int launch_stage_any(hg_hydro* H, int stage, const void* Uin, const void* U0, co
     L.U0 = U0;
     L.A = A;
     L.Uout = Uout;
+    if (H->prof) {
+        if (H->prof_used == kHydroProfPairs) {
+            int rc = hydro_prof_fold(H);
+            if (rc) return rc;
+        }
+        HG_CUDA(cudaEventRecord(H->prof_ev[2 * H->prof_used], H->stream));
+    }
     const cudaError_t e = H->dtype == HG_DT_F64 ? hg::hydro_stage_f64(L) : hg::hydro_stage_f32(L);
     ++H->launches;
     if (e != cudaSuccess) return hg::cuda_fail(e, "k_hydro_stage");
+    if (H->prof) {
+        HG_CUDA(cudaEventRecord(H->prof_ev[2 * H->prof_used + 1], H->stream));
+        ++H->prof_used;
+    }
     return HG_OK;
 }
 
@@ -193,6 +224,11 @@ void release(hg_hydro* H) {
     void* ptrs[] = {H->U, H->U1, H->A, H->staging, H->red, H->dres};
     for (void* p : ptrs)
         if (p) cudaFree(p);
+    if (H->prof_ev) {
+        for (int e = 0; e < 2 * kHydroProfPairs; ++e)
+            if (H->prof_ev[e]) cudaEventDestroy(H->prof_ev[e]);
+        delete[] H->prof_ev;
+    }
 }
 
 }  // namespace
@@ -349,6 +385,29 @@ int hg_hydro_virial(hg_hydro* H, hg_grid* g, double out[6]) {
 int hg_hydro_launches(hg_hydro* H, long long* n) {
     if (!H || !n) return fail(HG_ERR_ARG, "null argument");
     *n = H->launches;
+    return HG_OK;
+}
+
+int hg_hydro_profile(hg_hydro* H, int enable) {
+    int rc = check_hydro(H);
+    if (rc) return rc;
+    if (enable && !H->prof_ev) {
+        H->prof_ev = new cudaEvent_t[2 * kHydroProfPairs]();
+        for (int e = 0; e < 2 * kHydroProfPairs; ++e) HG_CUDA(cudaEventCreate(&H->prof_ev[e]));
+    }
+    if (!enable && (rc = hydro_prof_fold(H))) return rc;
+    H->prof = enable ? 1 : 0;
+    return HG_OK;
+}
+
+int hg_hydro_profile_read(hg_hydro* H, double* stage_ms, long long* stage_launches) {
+    int rc = check_hydro(H);
+    if (rc) return rc;
+    if ((rc = hydro_prof_fold(H))) return rc;
+    if (stage_ms) *stage_ms = H->prof_ms;
+    if (stage_launches) *stage_launches = H->prof_count;
+    H->prof_ms = 0.0;
+    H->prof_count = 0;
     return HG_OK;
 }
 

@@ -157,6 +157,14 @@ def test_launch_count_and_argument_checks():
     n0 = H.launches()
     H.step(1e-3)
     assert H.launches() - n0 == 2  # one launch per Runge-Kutta stage
+    H.profile(True)
+    for _ in range(3):
+        H.step(1e-3)
+    ms, nl = H.profile_read()
+    assert nl == 6 and ms > 0.0
+    H.profile(False)
+    H.step(1e-3)
+    assert H.profile_read() == (0.0, 0)
     with pytest.raises(hg.HGError):
         H.step(0.0)
     with pytest.raises(hg.HGError):
