@@ -9,7 +9,8 @@
 //
 // Kernel design (one launch per Runge-Kutta stage): a block owns a 32 x 8 column of cells and marches along z
 // through a chunk of planes.  A ring of primitive planes (the column plus a 2-cell halo in x and y) sits in
-// shared memory; each plane of the global state is read once per block and converted to primitives once.  Every
+// shared memory; each plane of the global state is read once per block and converted to primitives once (its
+// loads are issued before the current plane's face fluxes and consumed after them).  Every
 // face flux is evaluated once: the 33 x 8 x-faces and 32 x 9 y-faces of the current plane form one pool of work
 // over the block's threads and go to shared memory; the z-face above each cell is kept in registers and becomes
 // the next plane's lower face.  The update, the gravity source, the stage combination and the floors are fused
@@ -196,21 +197,45 @@ __device__ __forceinline__ void flux4(const Gas<T>& G, const T* c0, const T* c1,
     hllc<T, D>(G, wl, wr, F);
 }
 
-// stage plane p (clamped into the grid: the outgoing boundary's zero-gradient ghosts) of the column at (i0, j0)
+// Staging of plane p (clamped into the grid: the outgoing boundary's zero-gradient ghosts) of the column at
+// (i0, j0), in two halves so that the loads can be issued early and the conversion done later: plane_load reads
+// the conserved state of this thread's (at most two) cells of the staged plane into registers, plane_store
+// converts them to primitives and writes them to a ring slot.
+static_assert(PCELLS <= 2 * NT, "a thread stages at most two cells of a plane");
+
 template <typename T>
-__device__ __forceinline__ void stage_plane(T (*ws)[PCELLS], const StageArgs<T>& a, int i0, int j0, int p) {
+struct PlaneRegs {
+    T u[2][5];
+};
+
+template <typename T>
+__device__ __forceinline__ void plane_load(PlaneRegs<T>& r, const StageArgs<T>& a, int i0, int j0, int p) {
     const int kk = min(max(p, 0), a.nz - 1);
-    for (int c = threadIdx.x; c < PCELLS; c += NT) {
-        const int lx = c % PX, ly = c / PX;
-        const int i = min(max(i0 - HALO + lx, 0), a.nx - 1);
-        const int j = min(max(j0 - HALO + ly, 0), a.ny - 1);
-        const long long o = ((long long)kk * a.ny + j) * a.nx + i;
-        T u[5], w[5];
 #pragma unroll
-        for (int q = 0; q < 5; ++q) u[q] = __ldg(a.Uin + q * a.n + o);
-        cons_to_prim(a.gas.gm1, u, w);
+    for (int t = 0; t < 2; ++t) {
+        const int c = threadIdx.x + t * NT;
+        if (c < PCELLS) {
+            const int lx = c % PX, ly = c / PX;
+            const int i = min(max(i0 - HALO + lx, 0), a.nx - 1);
+            const int j = min(max(j0 - HALO + ly, 0), a.ny - 1);
+            const long long o = ((long long)kk * a.ny + j) * a.nx + i;
 #pragma unroll
-        for (int q = 0; q < 5; ++q) ws[q][c] = w[q];
+            for (int q = 0; q < 5; ++q) r.u[t][q] = __ldg(a.Uin + q * a.n + o);
+        }
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void plane_store(T (*ws)[PCELLS], const PlaneRegs<T>& r, T gm1) {
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+        const int c = threadIdx.x + t * NT;
+        if (c < PCELLS) {
+            T w[5];
+            cons_to_prim(gm1, r.u[t], w);
+#pragma unroll
+            for (int q = 0; q < 5; ++q) ws[q][c] = w[q];
+        }
     }
 }
 
@@ -237,7 +262,11 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 8 ? 2 : 3) k_hydro_stage(Stag
     const Gas<T> G = a.gas;
     using R = Ring<T>;
 
-    for (int p = k0 - 2; p <= k0 + 1; ++p) stage_plane(sm.w[R::slot(p)], a, i0, j0, p);
+    for (int p = k0 - 2; p <= k0 + 1; ++p) {
+        PlaneRegs<T> pr;
+        plane_load(pr, a, i0, j0, p);
+        plane_store(sm.w[R::slot(p)], pr, G.gm1);
+    }
     __syncthreads();
     T fzl[5], fzh[5];
     flux4<T, 2>(G, &sm.w[R::slot(k0 - 2)][0][cc], &sm.w[R::slot(k0 - 1)][0][cc], &sm.w[R::slot(k0)][0][cc],
@@ -259,8 +288,12 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 8 ? 2 : 3) k_hydro_stage(Stag
                 for (int q = 0; q < 3; ++q) acc[q] = __ldg(a.A + q * a.n + o);
             }
         }
-        stage_plane(sm.w[R::slot(k + 2)], a, i0, j0, k + 2);
-        if (!R::one_barrier) __syncthreads();
+        PlaneRegs<T> pr;
+        plane_load(pr, a, i0, j0, k + 2);  // with one barrier per plane, converted and stored after the x/y faces
+        if (!R::one_barrier) {
+            plane_store(sm.w[R::slot(k + 2)], pr, G.gm1);
+            __syncthreads();
+        }
         const int b = R::one_barrier ? (k & 1) : 0;
         const T(*W)[PCELLS] = sm.w[R::slot(k)];
         // x- and y-faces of plane k as one pool of NXF + NYF fluxes
@@ -284,6 +317,8 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 8 ? 2 : 3) k_hydro_stage(Stag
         if (!R::one_barrier)
             flux4<T, 2>(G, &sm.w[R::slot(k - 1)][0][cc], &sm.w[R::slot(k)][0][cc], &sm.w[R::slot(k + 1)][0][cc],
                         &sm.w[R::slot(k + 2)][0][cc], fzh);
+        else
+            plane_store(sm.w[R::slot(k + 2)], pr, G.gm1);
         __syncthreads();
         if (R::one_barrier)
             flux4<T, 2>(G, &sm.w[R::slot(k - 1)][0][cc], &sm.w[R::slot(k)][0][cc], &sm.w[R::slot(k + 1)][0][cc],
