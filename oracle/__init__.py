@@ -345,9 +345,15 @@ def hydro_virial(hg: HydroGrid, U, phi) -> dict:
 
 
 def coupled_step(og: Grid, phi: np.ndarray, phi_prev: np.ndarray, hg: HydroGrid, U: np.ndarray, dt: float,
-                 n_sub: int) -> None:
+                 n_sub: int, lmax: int = 0) -> None:
     """One hydro step with self-gravity (Sec. 2): the wave equation advanced n_sub sub-steps with rho = U[0] held
-    fixed, then the hydro step of dt with a = -grad phi of the advanced potential (both in place)."""
+    fixed, then the hydro step of dt with a = -grad phi of the advanced potential (both in place).  With Dirichlet
+    boundaries the ghost data of both time levels are first recomputed from the step's density by the multipole
+    expansion up to lmax (Sec. 4: the boundary values follow the current density)."""
+    if og.bc == BC_DIRICHLET:
+        Q = moments(og, U[0], lmax)
+        fill_multipole_ghosts(og, lmax, Q, phi)
+        fill_multipole_ghosts(og, lmax, Q, phi_prev)
     run(og, phi, phi_prev, U[0], n_sub)
     A = np.stack(accel(og, phi))
     hydro_step(hg, U, dt, A)

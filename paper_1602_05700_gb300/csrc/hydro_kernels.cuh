@@ -11,8 +11,8 @@
 // through a chunk of planes.  A ring of primitive planes (the column plus a 2-cell halo in x and y) sits in
 // shared memory; each plane of the global state is read once per block and converted to primitives once (its
 // loads are issued before the current plane's face fluxes and consumed after them).  Every
-// face flux is evaluated once: the 33 x 8 x-faces and 32 x 9 y-faces of the current plane form one pool of work
-// over the block's threads and go to shared memory; the z-face above each cell is kept in registers and becomes
+// face flux is evaluated once: the 33 x 8 x-faces and 32 x 9 y-faces of the current plane are computed by the
+// block's threads in two full rounds and one round of two warps, into shared memory; the z-face above each cell is kept in registers and becomes
 // the next plane's lower face.  The update, the gravity source, the stage combination and the floors are fused
 // into the same pass, so a stage reads the stage state (and, for stage 2, the step's initial state and a) once
 // and writes the new state once.
@@ -296,22 +296,28 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 8 ? 2 : 3) k_hydro_stage(Stag
         }
         const int b = R::one_barrier ? (k & 1) : 0;
         const T(*W)[PCELLS] = sm.w[R::slot(k)];
-        // x- and y-faces of plane k as one pool of NXF + NYF fluxes
-        for (int f = tid; f < NXF + NYF; f += NT) {
+        // x- and y-faces of plane k: x-face tx of row ty (between cells tx-1 and tx), the y-face below cell
+        // (tx, ty), then the last x-face of each row (warp 1, lanes 0-7) and the y-faces above row TY-1 (warp 0)
+        {
             T F[5];
-            if (f < NXF) {
-                const int row = f / (TX + 1), af = f - row * (TX + 1);
-                const int c0 = (row + HALO) * PX + af;  // cells af-2 .. af+1 of the row: the face between af-1, af
-                flux4<T, 0>(G, &W[0][c0], &W[0][c0 + 1], &W[0][c0 + 2], &W[0][c0 + 3], F);
+            const int c0 = (ty + HALO) * PX + tx;  // cells tx-2 .. tx+1 of row ty
+            flux4<T, 0>(G, &W[0][c0], &W[0][c0 + 1], &W[0][c0 + 2], &W[0][c0 + 3], F);
 #pragma unroll
-                for (int q = 0; q < 5; ++q) sm.fx[b][q][f] = F[q];
-            } else {
-                const int g = f - NXF;
-                const int fj = g / TX, col = g - fj * TX;
-                const int c0 = fj * PX + col + HALO;  // rows fj-2 .. fj+1 of the column: the face between fj-1, fj
-                flux4<T, 1>(G, &W[0][c0], &W[0][c0 + PX], &W[0][c0 + 2 * PX], &W[0][c0 + 3 * PX], F);
+            for (int q = 0; q < 5; ++q) sm.fx[b][q][ty * (TX + 1) + tx] = F[q];
+            const int c1 = ty * PX + tx + HALO;  // rows ty-2 .. ty+1 of column tx
+            flux4<T, 1>(G, &W[0][c1], &W[0][c1 + PX], &W[0][c1 + 2 * PX], &W[0][c1 + 3 * PX], F);
 #pragma unroll
-                for (int q = 0; q < 5; ++q) sm.fy[b][q][g] = F[q];
+            for (int q = 0; q < 5; ++q) sm.fy[b][q][ty * TX + tx] = F[q];
+            if (ty == 0) {
+                const int c2 = TY * PX + tx + HALO;  // rows TY-2 .. TY+1: the face between rows TY-1 and TY
+                flux4<T, 1>(G, &W[0][c2], &W[0][c2 + PX], &W[0][c2 + 2 * PX], &W[0][c2 + 3 * PX], F);
+#pragma unroll
+                for (int q = 0; q < 5; ++q) sm.fy[b][q][TY * TX + tx] = F[q];
+            } else if (ty == 1 && tx < TY) {
+                const int c3 = (tx + HALO) * PX + TX;  // row tx, cells TX-2 .. TX+1: the face between TX-1 and TX
+                flux4<T, 0>(G, &W[0][c3], &W[0][c3 + 1], &W[0][c3 + 2], &W[0][c3 + 3], F);
+#pragma unroll
+                for (int q = 0; q < 5; ++q) sm.fx[b][q][tx * (TX + 1) + TX] = F[q];
             }
         }
         if (!R::one_barrier)

@@ -137,6 +137,37 @@ def test_fp64_coupled_step_bit_exact(n):
     assert v["rho_max"] == w["rho_max"]
 
 
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-10), ("f32k", 1e-4)])
+def test_coupled_step_with_multipole_dirichlet_gravity(prec, tol):
+    """The coupling with the other outer boundary of the paper (Dirichlet data by the multipole expansion, l <= 4,
+    recomputed from each hydro step's density): FP64 to rounding (the moments' sums run in another order), FP32
+    compensated within its tolerance."""
+    n, lmax, kg, cfl = 32, 4, 5.0, 0.3
+    h = 1.0 / n
+    rho, P, phi, info = I.polytrope(n, pert=0.01, seed=6)
+    W = np.zeros((5, n, n, n))
+    W[0], W[4] = rho, P
+    W[1] = 0.05  # a bulk drift, so the moments change from step to step
+    hgo = O.HydroGrid(n, n, n, h, GAMMA, 0.5 * info["rho_atm"], 0.5 * info["p_atm"])
+    U = O.hydro_cons(hgo, W)
+    c = kg * O.hydro_max_speed(hgo, U)
+    dtg = cfl * h / (c * np.sqrt(3.0))
+    og = O.Grid(n, n, n, h, (-0.5, -0.5, -0.5), c, 1.0, dtg, O.BC_DIRICHLET)
+    p, q = O.initial_state(og, rho, lmax=lmax, phi0=phi, phi_prev0=phi)
+    g = hg.Grid(n, n, n, h, (-0.5, -0.5, -0.5), c, 1.0, dtg, prec, "multipole", lmax)
+    g.set_density(torch.from_numpy(rho).cuda())
+    g.set_phi(torch.from_numpy(phi).cuda())
+    H = hg.Hydro(n, n, n, h, GAMMA, hgo.rho_floor, hgo.p_floor, dtype="f64" if prec == "f64" else "f32")
+    H.set_primitive(torch.from_numpy(W).cuda())
+    nsub = 8
+    for _ in range(3):
+        H.step(nsub * dtg, g, nsub)
+        O.coupled_step(og, p, q, hgo, U, nsub * dtg, nsub, lmax)
+    assert rel_err(H.state("cpu").numpy(), U) < tol
+    ph = g.phi_ghosted()
+    assert np.abs(ph - p).max() < tol * np.abs(p).max()
+
+
 def test_fp32_coupled_step_within_tolerance():
     n = 40
     g, H, og, p, q, hgo, U, dtg, phi0 = coupled_setup(n, "f32k", pert=0.01, seed=4)
