@@ -375,7 +375,7 @@ def run_reference(args):
             "e2e": {"value": round(v, 5), "unit": "Gcell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
-# ---- the other workloads (reported in the design doc; the default run above is the headline) --------------------------
+# ---- the other workloads (the default run above is the headline) -----------------------------------------------------
 
 def run_precision(args):
     """Config 2: 256^3 sphere + 8 blobs (seed 1), multipole boundary l <= 4, 2000 sub-steps in FP32-compensated and
