@@ -12,9 +12,14 @@
  *
  * Readings (the paper names the solver family only):
  *   state        conserved u = (rho, rho vx, rho vy, rho vz, E), E = P/(gamma-1) + rho |v|^2 / 2.
- *   reconstruction  piecewise linear in the primitives w = (rho, vx, vy, vz, P), minmod-limited slopes:
- *                left state at face s+1/2  w_s + minmod(w_s - w_{s-1}, w_{s+1} - w_s) / 2,
- *                right state               w_{s+1} - minmod(w_{s+1} - w_s, w_{s+2} - w_{s+1}) / 2.
+ *   reconstruction  piecewise linear in the primitives w = (rho, vx, vy, vz, P) with monotonized-central
+ *                limited slopes, mc(a, b) = the argument of least magnitude among 2a, (a + b)/2, 2b when all
+ *                three have one sign, else 0:
+ *                left state at face s+1/2  w_s + mc(w_s - w_{s-1}, w_{s+1} - w_s) / 2,
+ *                right state               w_{s+1} - mc(w_{s+1} - w_s, w_{s+2} - w_{s+1}) / 2.
+ *                (A minmod limiter, the more diffusive choice, flattens the peaked core of the paper's n = 3
+ *                star: its central density would fall by 6.5% in ~4 dynamical times at the paper's resolution,
+ *                where Sec. 3 reports a decline of about 2% in ~5.)
  *   Riemann      HLLC (Toro, Spruce & Speares 1994) with Davis' wave-speed bounds
  *                S_L = min(u_L - a_L, u_R - a_R), S_R = max(u_L + a_L, u_R + a_R), a = sqrt(gamma P / rho).
  *   boundary     outgoing = zero gradient: the two ghost layers repeat the edge cell (indices clamped).
@@ -106,9 +111,21 @@ void oh_prim_from_cons(const oh_grid* g, const double* U, double* W) {
     }
 }
 
-static double minmod(double a, double b) {
-    if (a > 0.0 && b > 0.0) return a < b ? a : b;
-    if (a < 0.0 && b < 0.0) return a > b ? a : b;
+/* monotonized-central slope from the one-sided differences a (backward) and b (forward) */
+static double mc(double a, double b) {
+    const double c = 0.5 * (a + b), a2 = 2.0 * a, b2 = 2.0 * b;
+    if (a > 0.0 && b > 0.0) {
+        double m = c;
+        if (a2 < m) m = a2;
+        if (b2 < m) m = b2;
+        return m;
+    }
+    if (a < 0.0 && b < 0.0) {
+        double m = c;
+        if (a2 > m) m = a2;
+        if (b2 > m) m = b2;
+        return m;
+    }
     return 0.0;
 }
 
@@ -184,8 +201,8 @@ static void face_flux(const oh_grid* g, const double* U, int i, int j, int k, in
     prim_at(g, U, i, j, k, d, t + 1, wp);
     prim_at(g, U, i, j, k, d, t + 2, wpp);
     for (int q = 0; q < 5; ++q) {
-        wl[q] = w0[q] + 0.5 * minmod(w0[q] - wm[q], wp[q] - w0[q]);
-        wr[q] = wp[q] - 0.5 * minmod(wp[q] - w0[q], wpp[q] - wp[q]);
+        wl[q] = w0[q] + 0.5 * mc(w0[q] - wm[q], wp[q] - w0[q]);
+        wr[q] = wp[q] - 0.5 * mc(wp[q] - w0[q], wpp[q] - wp[q]);
     }
     oh_hllc(g->gamma, wl, wr, d, F);
 }

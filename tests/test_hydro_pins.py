@@ -6,7 +6,7 @@ as the source -rho grad phi) and of the polytrope input, against what mathematic
 * the same 1-D problem along x, y and z gives bit-identical fields   -> transposed strides, per-axis velocity
 * HLLC: consistency F(w, w) = physical flux, upwinding for supersonic states, an isolated stationary contact kept
   to rounding (an HLL flux would smear it)                            -> the star states and the contact speed
-* smooth advection converges at second order                          -> limiter and two-stage integrator
+* smooth advection converges at second order (error ratio > 3.5 per halving) -> limiter, two-stage integrator
 * conservation of mass, momentum and energy to rounding                -> flux differencing, boundary
 * uniform field on a uniform gas: exact Heun response m = rho a dt, E - E0 = rho |a|^2 dt^2 / 2 -> source terms
 * characteristic speed of a hand-computed state                       -> the c_g normalisation
@@ -108,7 +108,7 @@ def test_sod_against_exact_solution_converges(axis):
         others = [q for q in (1, 2, 3) if q != 1 + axis]
         assert np.all(W[others] == 0.0)
     errs = np.array(errs)
-    assert np.all(errs[0] < [1e-2, 2e-2, 8e-3]), errs[0]
+    assert np.all(errs[0] < [6e-3, 1.2e-2, 4.5e-3]), errs[0]  # MC slopes (minmod: 7.7e-3, 1.5e-2, 6.2e-3)
     # discontinuities limit the L1 rate to about 1 (shock, contact) and 2/3..1 (contact smearing)
     assert np.all(errs[1] < 0.75 * errs[0]) and np.all(errs[2] < 0.75 * errs[1]), errs
 
@@ -181,7 +181,7 @@ def test_smooth_advection_is_second_order():
         rho = U[0].ravel()
         keep = (x > 0.3) & (x < 0.95)  # away from the inflow edge, whose zero-gradient ghosts are not periodic
         errs.append(np.abs(rho - (1.0 + 0.2 * np.sin(2 * np.pi * (x - 0.1))))[keep].mean())
-    assert errs[1] / errs[2] > 2.8 and errs[0] / errs[1] > 2.8, errs
+    assert errs[1] / errs[2] > 3.5 and errs[0] / errs[1] > 3.5, errs
 
 
 def test_conservation_to_rounding():
