@@ -704,23 +704,24 @@ def run_virial(args):
     """The paper's 3D star (Sec. 2; Sec. 3, Eq. VC): an n = 3 polytrope (M = 1, R = 1/3, G = 1) at the centre of
     [-1/2, 1/2]^3 on N^3 cells (the paper's 140^3 octant of a domain 1.5 R wide, mirrored: N = 280), gamma = 5/3, a
     dilute atmosphere of 1e-6 rho_c, evolved by the coupled GPU step (FP32 hydro, compensated-FP32 gravity, Robin
-    boundary) for `substeps` hydro steps with k_g = 5 and Courant number 0.3 for both parts (c_g fixed from the
-    initial max(c_s + |v|); each hydro step the largest multiple of the gravity sub-step within its own Courant
-    limit); unperturbed and with 1% random density perturbations.  Reports VC and rho_max / rho_max(0) against
-    time, and the time of a coupled hydro step split into its gravity and hydro parts."""
+    boundary) for `substeps` hydro steps with Courant number 0.3 for both parts (c_g = k_g max(c_s + |v|) fixed
+    from the initial state; each hydro step the largest multiple of the gravity sub-step within its own Courant
+    limit): k_g = 5 unperturbed and with 1% random density perturbations (the paper's H models), and k_g = 20
+    unperturbed (closer to the instantaneous-Poisson limit k_g -> infinity).  Reports VC and rho_max / rho_max(0)
+    against time, and the time of a coupled hydro step split into its gravity and hydro parts."""
     import numpy as np
     import torch
 
     import paper_1602_05700_gb300 as hg
     from paper_1602_05700_gb300 import inputs as I
 
-    n, steps, kg, cfl = args.n, args.substeps, 5.0, 0.3
+    n, steps, cfl = args.n, args.substeps, 0.3
     h = 1.0 / n
     t_dyn = (1.0 / 3.0) ** 1.5  # sqrt(R^3 / (G M))
-    res = {"workload": f"{n}^3 n=3 polytrope (M 1, R 1/3), gamma 5/3, Robin gravity, k_g {kg:g}, Courant {cfl:g}, "
+    res = {"workload": f"{n}^3 n=3 polytrope (M 1, R 1/3), gamma 5/3, Robin gravity, Courant {cfl:g}, "
                        f"{steps} hydro steps", "t_dyn": t_dyn}
     ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
-    for label, pert in (("unperturbed", 0.0), ("perturbed_1pct", 0.01)):
+    for label, pert, kg in (("unperturbed", 0.0, 5.0), ("perturbed_1pct", 0.01, 5.0), ("unperturbed_kg20", 0.0, 20.0)):
         rho, P, phi, info = I.polytrope(n, pert=pert, seed=21)
         W = np.zeros((5, n, n, n), np.float32)
         W[0], W[4] = rho, P
@@ -753,7 +754,7 @@ def run_virial(args):
         stage_ms, stage_n = H.profile_read()
         H.profile(False)
         vc = np.array([r[1] for r in trace])
-        res[label] = {"t_end_over_t_dyn": round(t / t_dyn, 3), "substeps_per_hydro_step": nsub,
+        res[label] = {"k_g": kg, "t_end_over_t_dyn": round(t / t_dyn, 3), "substeps_per_hydro_step": nsub,
                       "VC_initial": trace[0][1], "VC_final": trace[-1][1],
                       "VC_max_abs": float(np.abs(vc).max()), "VC_max_abs_after_1_t_dyn":
                       max((abs(r[1]) for r in trace if r[0] >= 1.0), default=None),

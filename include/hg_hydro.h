@@ -10,8 +10,9 @@
  *
  *   state        conserved u = (rho, rho vx, rho vy, rho vz, E), E = P/(gamma-1) + rho |v|^2 / 2, on the same
  *                nx*ny*nz cells as the gravity grid;
- *   fluxes       piecewise-linear primitives (rho, v, P) with minmod-limited slopes, HLLC fluxes with Davis'
- *                wave-speed bounds, faces of all three axes in one unsplit update;
+ *   fluxes       piecewise-linear primitives (rho, v, P) with monotonized-central limited slopes (the
+ *                least-magnitude of 2a, (a+b)/2, 2b for one-sided differences a, b of one sign, else 0), HLLC
+ *                fluxes with Davis' wave-speed bounds, faces of all three axes in one unsplit update;
  *   boundary     outgoing (zero gradient: two ghost layers repeat the edge cell);
  *   time         two-stage SSP Runge-Kutta (Heun), each stage L(u) = -div F / h + (0, rho a, m . a);
  *   gravity      a = -grad phi of the wave solution after the step's k_g sub-steps, held over the hydro step;

@@ -3,8 +3,8 @@
 // contraction and approximate division and square root).  Everything here has internal linkage, so each
 // translation unit keeps its own instance with its own floating-point flags.
 //
-// Scheme (paper Sec. 2; the library's reading, fixed by the ABI header): minmod-limited piecewise-linear
-// primitives, HLLC fluxes with Davis' wave-speed bounds, outgoing (zero-gradient) boundaries, two-stage SSP
+// Scheme (paper Sec. 2; the library's reading, fixed by the ABI header): piecewise-linear primitives with
+// monotonized-central limited slopes, HLLC fluxes with Davis' wave-speed bounds, outgoing (zero-gradient) boundaries, two-stage SSP
 // Runge-Kutta with the gravity source (0, rho a, m . a), floors after each stage.
 //
 // Kernel design (one launch per Runge-Kutta stage): a block owns a 32 x 8 column of cells and marches along z
@@ -133,6 +133,14 @@ __device__ __forceinline__ float minmod(float a, float b) {
     return fmaxf(fminf(a, b), fminf(fmaxf(a, b), 0.0f));  // the median of (a, b, 0)
 }
 
+// monotonized-central slope from the one-sided differences a (backward) and b (forward): the argument of least
+// magnitude among 2a, (a + b)/2, 2b when all three have one sign, else 0 -- written as minmod((a + b)/2,
+// 2 minmod(a, b)), which selects the same element (every candidate is computed exactly as in the three-way form)
+template <typename T>
+__device__ __forceinline__ T mc_slope(T a, T b) {
+    return minmod(T(0.5) * (a + b), T(2) * minmod(a, b));
+}
+
 // conserved state u and physical flux f along axis D of the primitive state w
 template <typename T, int D>
 __device__ __forceinline__ void state_flux(T gm1, const T w[5], T u[5], T f[5]) {
@@ -184,15 +192,15 @@ __device__ __forceinline__ void hllc(const Gas<T>& G, const T wl[5], const T wr[
 }                                                                                    // supersonic face is never used
 
 // flux through the face between cells c1 and c2 of the four consecutive staged cells c0..c3 (component stride
-// PCELLS): minmod-limited left and right states, then HLLC along axis D
+// PCELLS): MC-limited left and right states, then HLLC along axis D
 template <typename T, int D>
 __device__ __forceinline__ void flux4(const Gas<T>& G, const T* c0, const T* c1, const T* c2, const T* c3, T F[5]) {
     T wl[5], wr[5];
 #pragma unroll
     for (int q = 0; q < 5; ++q) {
         const T a = c0[q * PCELLS], b = c1[q * PCELLS], c = c2[q * PCELLS], d = c3[q * PCELLS];
-        wl[q] = b + T(0.5) * minmod(b - a, c - b);
-        wr[q] = c - T(0.5) * minmod(c - b, d - c);
+        wl[q] = b + T(0.5) * mc_slope(b - a, c - b);
+        wr[q] = c - T(0.5) * mc_slope(c - b, d - c);
     }
     hllc<T, D>(G, wl, wr, F);
 }
