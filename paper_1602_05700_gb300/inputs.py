@@ -15,8 +15,9 @@ Recipes (unit cube [-1/2, 1/2]^3, N cells per side, cell-centred):
   noise        i.i.d. uniform values for stencil-parity inputs (the stencil is checked on arbitrary data).
   polytrope    the 3D star of the paper's virial test (Sec. 2): a Lane-Emden polytrope of index n (default 3)
                with mass M and radius R at the origin, point-sampled at cell centres, v = 0, P = K rho^(1+1/n),
-               a dilute atmosphere (rho = atm * rho_c, P from the same K) outside, optional i.i.d. relative
-               density perturbations inside the star, and its exact potential for seeding phi.
+               plus a dilute isothermal atmosphere in hydrostatic equilibrium with the star's potential (density
+               atm * rho_c at the surface, sound speed squared atm_kt * G M / R), optional i.i.d. relative density
+               perturbations inside the star, and the star's exact potential for seeding phi.
   hydro states primitive fields (rho, vx, vy, vz, P): shock tubes along an axis and i.i.d. bounded noise.
 """
 from __future__ import annotations
@@ -203,14 +204,19 @@ def _hermite(xs, ts, ds, x):
 
 
 def polytrope(nx: int, n_index: float = 3.0, mass: float = 1.0, radius: float = 1.0 / 3.0, G: float = 1.0,
-              atm: float = 1e-6, pert: float = 0.0, seed: int = 0, ny: int | None = None, nz: int | None = None,
-              h: float | None = None, lo: float = -0.5):
+              atm: float = 1e-6, atm_kt: float = 0.5, pert: float = 0.0, seed: int = 0, ny: int | None = None,
+              nz: int | None = None, h: float | None = None, lo: float = -0.5):
     """Polytropic star at the origin: returns (rho, P, phi, info), each field (nz, ny, nx) float64.
 
-    rho = rho_c theta^n(r / alpha) with alpha = R / xi_1 and rho_c = M / (4 pi alpha^3 omega); P = K rho^(1+1/n)
+    Star: rho_c theta^n(r / alpha) with alpha = R / xi_1 and rho_c = M / (4 pi alpha^3 omega); P = K rho^(1+1/n)
     with K = 4 pi G alpha^2 rho_c^(1-1/n) / (n+1); exact potential -G M / R - (n+1) K rho_c^(1/n) theta inside,
-    -G M / r outside.  Outside the star (and wherever rho_c theta^n < atm rho_c) rho = atm rho_c, P = K rho^(1+1/n).
+    -G M / r outside.
+    Atmosphere (a "dilute atmosphere" of negligible mass, Sec. 2): an isothermal component with P_a = k_T rho_a,
+    k_T = atm_kt G M / R, in hydrostatic equilibrium with that potential everywhere, rho_a = atm rho_c
+    exp(-(phi - phi(R)) / k_T), added to the star's density and pressure (both components balance gravity on their
+    own, so the sum does too, and the atmosphere does not fall onto the star).  atm = 0: no atmosphere.
     pert > 0 multiplies rho inside the star by 1 + pert u, u ~ U[-1, 1] from PCG64(seed) (P is left unchanged).
+    phi is the star's potential; the atmosphere's own gravity (its mass is ~6e-4 M for the defaults) is left out.
     """
     ny = ny or nx
     nz = nz or nx
@@ -226,16 +232,20 @@ def polytrope(nx: int, n_index: float = 3.0, mass: float = 1.0, radius: float = 
     inside = r < radius
     theta = np.zeros_like(r)
     theta[inside] = np.maximum(_hermite(xs_, ts_, ds_, r[inside] / alpha), 0.0)
-    rho_atm = atm * rho_c
-    rho = np.maximum(rho_c * theta ** n_index, rho_atm)
+    rho = rho_c * theta ** n_index
     if pert > 0.0:
         u = noise(r.shape, seed, -1.0, 1.0)
-        rho = np.where(inside & (rho > rho_atm), rho * (1.0 + pert * u), rho)
-    P = K * np.maximum(rho_c * theta ** n_index, rho_atm) ** (1.0 + 1.0 / n_index)
+        rho = np.where(inside, rho * (1.0 + pert * u), rho)
+    P = K * (rho_c * theta ** n_index) ** (1.0 + 1.0 / n_index)
     phi = np.where(inside, -G * mass / radius - (n_index + 1.0) * K * rho_c ** (1.0 / n_index) * theta,
                    -G * mass / np.maximum(r, 1e-300))
-    info = dict(rho_c=rho_c, K=K, alpha=alpha, xi1=xi1, omega=omega, rho_atm=rho_atm,
-                p_atm=K * rho_atm ** (1.0 + 1.0 / n_index))
+    kt = atm_kt * G * mass / radius
+    rho_a = atm * rho_c * np.exp(-(phi + G * mass / radius) / kt) if atm > 0.0 else np.zeros_like(r)
+    rho = rho + rho_a
+    P = P + kt * rho_a
+    rho_min = float(rho_a.min()) if atm > 0.0 else 0.0
+    info = dict(rho_c=rho_c, K=K, alpha=alpha, xi1=xi1, omega=omega, kt=kt, rho_atm=rho_min, p_atm=kt * rho_min,
+                atm_mass=float(rho_a.sum()) * h ** 3)
     return rho, P, phi, info
 
 
