@@ -842,7 +842,7 @@ def main():
     hg.build()
     if args.config != "headline":
         defaults = {"precision": (256, 2000), "batch": (0, 500), "adjoint": (128, 400), "lag": (128, 40),
-                    "domain": (0, 40), "virial": (280, 1900)}
+                    "domain": (0, 40), "virial": (280, 2600)}
         n0, t0 = defaults[args.config]
         if args.n == 512 and n0:
             args.n = n0
