@@ -10,12 +10,12 @@
 // Kernel design (one launch per Runge-Kutta stage): a block owns a 32 x 8 column of cells and marches along z
 // through a chunk of planes.  A ring of primitive planes (the column plus a 2-cell halo in x and y) sits in
 // shared memory; each plane of the global state is read once per block and converted to primitives once (its
-// loads are issued before the current plane's face fluxes and consumed after them).  Every
-// face flux is evaluated once: the 33 x 8 x-faces and 32 x 9 y-faces of the current plane are computed by the
-// block's threads in two full rounds and one round of two warps, into shared memory; the z-face above each cell is kept in registers and becomes
-// the next plane's lower face.  The update, the gravity source, the stage combination and the floors are fused
-// into the same pass, so a stage reads the stage state (and, for stage 2, the step's initial state and a) once
-// and writes the new state once.
+// loads are issued before the current plane's face fluxes and consumed after them).  Every face flux is evaluated
+// once: the 33 x 8 x-faces and 32 x 9 y-faces of the current plane are computed by the block's threads in two full
+// rounds and one round of two warps, into shared memory; the z-face above each cell is kept in registers and
+// becomes the next plane's lower face, and the z-slope of its upper cell is kept for the next z-face.  The update,
+// the gravity source, the stage combination and the floors are fused into the same pass, so a stage reads the
+// stage state (and, for stage 2, the step's initial state and a) once and writes the new state once.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -205,6 +205,33 @@ __device__ __forceinline__ void flux4(const Gas<T>& G, const T* c0, const T* c1,
     hllc<T, D>(G, wl, wr, F);
 }
 
+// z-face between planes k and k+1 of this thread's column: the limited slope of plane k (carried from the
+// previous plane, where it was the upper cell's slope) and that of plane k+1 (computed here from planes k, k+1,
+// k+2 and carried on); the same operations on the same values as flux4, each slope evaluated once
+template <typename T>
+__device__ __forceinline__ void zflux(const Gas<T>& G, const T* ck, const T* ck1, const T* ck2, const T sk[5],
+                                      T sk1[5], T F[5]) {
+    T wl[5], wr[5];
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+        const T b = ck[q * PCELLS], c = ck1[q * PCELLS], d = ck2[q * PCELLS];
+        sk1[q] = mc_slope(c - b, d - c);
+        wl[q] = b + T(0.5) * sk[q];
+        wr[q] = c - T(0.5) * sk1[q];
+    }
+    hllc<T, 2>(G, wl, wr, F);
+}
+
+// limited slope of this thread's cell in plane p from planes p-1, p, p+1
+template <typename T>
+__device__ __forceinline__ void zslope(const T* cm, const T* c0, const T* cp, T s[5]) {
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+        const T a = cm[q * PCELLS], b = c0[q * PCELLS], c = cp[q * PCELLS];
+        s[q] = mc_slope(b - a, c - b);
+    }
+}
+
 // Staging of plane p (clamped into the grid: the outgoing boundary's zero-gradient ghosts) of the column at
 // (i0, j0), in two halves so that the loads can be issued early and the conversion done later: plane_load reads
 // the conserved state of this thread's (at most two) cells of the staged plane into registers, plane_store
@@ -276,9 +303,11 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 8 ? 2 : 3) k_hydro_stage(Stag
         plane_store(sm.w[R::slot(p)], pr, G.gm1);
     }
     __syncthreads();
-    T fzl[5], fzh[5];
-    flux4<T, 2>(G, &sm.w[R::slot(k0 - 2)][0][cc], &sm.w[R::slot(k0 - 1)][0][cc], &sm.w[R::slot(k0)][0][cc],
-                &sm.w[R::slot(k0 + 1)][0][cc], fzl);
+    T fzl[5], fzh[5], szk[5], szk1[5];  // z-faces below and above plane k; z-slopes of planes k and k+1
+    zslope(&sm.w[R::slot(k0 - 2)][0][cc], &sm.w[R::slot(k0 - 1)][0][cc], &sm.w[R::slot(k0)][0][cc], szk);
+    zflux(G, &sm.w[R::slot(k0 - 1)][0][cc], &sm.w[R::slot(k0)][0][cc], &sm.w[R::slot(k0 + 1)][0][cc], szk, szk1, fzl);
+#pragma unroll
+    for (int q = 0; q < 5; ++q) szk[q] = szk1[q];
     if (!R::one_barrier) __syncthreads();  // with four slots, plane k0-2's slot is refilled next
 
     for (int k = k0; k < k1; ++k) {
@@ -329,14 +358,14 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 8 ? 2 : 3) k_hydro_stage(Stag
             }
         }
         if (!R::one_barrier)
-            flux4<T, 2>(G, &sm.w[R::slot(k - 1)][0][cc], &sm.w[R::slot(k)][0][cc], &sm.w[R::slot(k + 1)][0][cc],
-                        &sm.w[R::slot(k + 2)][0][cc], fzh);
+            zflux(G, &sm.w[R::slot(k)][0][cc], &sm.w[R::slot(k + 1)][0][cc], &sm.w[R::slot(k + 2)][0][cc], szk, szk1,
+                  fzh);
         else
             plane_store(sm.w[R::slot(k + 2)], pr, G.gm1);
         __syncthreads();
         if (R::one_barrier)
-            flux4<T, 2>(G, &sm.w[R::slot(k - 1)][0][cc], &sm.w[R::slot(k)][0][cc], &sm.w[R::slot(k + 1)][0][cc],
-                        &sm.w[R::slot(k + 2)][0][cc], fzh);
+            zflux(G, &sm.w[R::slot(k)][0][cc], &sm.w[R::slot(k + 1)][0][cc], &sm.w[R::slot(k + 2)][0][cc], szk, szk1,
+                  fzh);
         if (own) {
             T r[5], un[5];
 #pragma unroll
@@ -362,7 +391,10 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 8 ? 2 : 3) k_hydro_stage(Stag
             for (int q = 0; q < 5; ++q) a.Uout[q * a.n + o] = un[q];
         }
 #pragma unroll
-        for (int q = 0; q < 5; ++q) fzl[q] = fzh[q];
+        for (int q = 0; q < 5; ++q) {
+            fzl[q] = fzh[q];
+            szk[q] = szk1[q];
+        }
     }
 }
 
