@@ -87,8 +87,9 @@ def test_fp64_floors_bit_exact():
     assert U[0].min() >= 1e-3
 
 
-def test_fp32_hydro_steps_within_tolerance():
-    shape = (23, 19, 37)
+@pytest.mark.parametrize("shape", [(23, 19, 37), (1, 1, 1), (1, 1, 64), (40, 1, 1), (1, 33, 1), (3, 2, 33),
+                                   (17, 9, 100)])
+def test_fp32_hydro_steps_within_tolerance(shape):
     H, hgo = pair(shape, "f32")
     W = I.hydro_noise(shape, 77)
     H.set_primitive(W)
