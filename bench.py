@@ -48,6 +48,11 @@ def workload(n):
     return dict(n=n, h=h, v_max=v_max, c=c, dt_hyd=dt_hyd, dt=dt_hyd / N_SUB, origin=(-0.5, -0.5, -0.5), G=1.0)
 
 
+def workload_name(n):
+    return (f"{n}^3 unit cube, two orbiting Gaussian blobs (sigma 0.05, mass 1, r 0.15, omega 2pi), Robin boundary, "
+            f"c_h = 10 v_max, {N_SUB} sub-steps per hydro step; per step set_density + {N_SUB} sub-steps + -grad phi")
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -246,10 +251,7 @@ def run_ours(args, rank, world, local_rank):
         "value": round(value, 3), "unit": "Gcell-updates/s", "n_gpus": world, "steps": steps, "warmup": warm,
         "ms_per_step": round(res["ms"] / steps, 4), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32" if args.prec == "f32k" else "f64", "data": "synthetic",
-        "config": {"workload": f"{n}^3 unit cube, two orbiting Gaussian blobs (sigma 0.05, mass 1, r 0.15, omega 2pi), "
-                               f"Robin boundary, c_h = 10 v_max, {N_SUB} sub-steps per hydro step; per step "
-                               "set_density + 20 sub-steps + -grad phi",
-                   "grid": [n, n, n], "substeps_per_step": N_SUB,
+        "config": {"workload": workload_name(n), "grid": [n, n, n], "substeps_per_step": N_SUB,
                    "precision": "f32 compensated (Kahan)" if args.prec == "f32k" else "f64",
                    "temporal_depth": best, "depth_sweep_gcells": sweep,
                    "parallelism": f"{world} independent grids (one per GPU)",
@@ -368,8 +370,8 @@ def run_reference(args):
             "value": round(v, 5), "unit": "Gcell-updates/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(sec / args.steps * 1e3, 3), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"{n}^3 unit cube, two orbiting Gaussian blobs, Robin boundary (oracle sample)",
-                       "grid": [n, n, n]},
+            "config": {"workload": workload_name(n), "grid": [n, n, n], "substeps_per_step": N_SUB,
+                       "precision": "f64 (the oracle)", "parallelism": "1 process, 1 host core"},
             "cpu_baseline": {"value": round(v, 5), "unit": "Gcell-updates/s", "cores": 1, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": round(v, 5), "unit": "Gcell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
