@@ -8,9 +8,6 @@
 // stage kernel is instantiated in hydro_f32.cu with contraction on.
 #include <cuda_runtime.h>
 #include <math.h>
-#include <stdio.h>
-
-#include <vector>
 
 #include "hg_hydro.h"
 #include "hg_internal.cuh"
