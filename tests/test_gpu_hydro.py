@@ -207,6 +207,20 @@ def test_launch_count_and_argument_checks():
         H.set_primitive(np.zeros((5, 8, 8, 7)))
 
 
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+def test_state_round_trip_host_and_device(dtype):
+    shape = (5, 6, 7)
+    H, hgo = pair(shape, dtype)
+    tdt = torch.float32 if dtype == "f32" else torch.float64
+    U = torch.from_numpy(O.hydro_cons(hgo, I.hydro_noise(shape, 3))).to(tdt)
+    H.set_state(U.numpy())                 # from host
+    assert torch.equal(H.state("cpu"), U)
+    H.set_state((2 * U).cuda())            # from device
+    assert torch.equal(H.state("cuda").cpu(), 2 * U)
+    with pytest.raises(hg.HGError):
+        H.virial(hg.Grid.unit_cube(8))     # grid size mismatch
+
+
 def test_full_size_sampled_cells_bit_exact():
     """280^3 polytrope (the virial workload's grid) with 1% density perturbations, one FP64 hydro step in the
     launch configuration of the benchmark; 40 sampled cells against the oracle on the 9^3 neighbourhood each
