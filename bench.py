@@ -239,7 +239,7 @@ def run_ours(args, rank, world, local_rank):
         sweep = None
     else:
         sweep = {}
-        for d in range(1, 5):
+        for d in range(1, 9):
             sweep[d] = round(rate(measure("f32k", d, 3)), 2)
         best = max(sweep, key=sweep.get)
     if args.prec == "f64":  # the FP64 mode as the profiled headline (e.g. to capture its kernel alone)

@@ -117,7 +117,7 @@ int hg_step(hg_grid* g, int n_substeps);
  * 2..HG_MAX_TEMPORAL_DEPTH advances k sub-steps per round trip through HBM (rho is frozen across them, Sec. 2).
  * Results are the same as k single sweeps.  HG_ERR_ARG for k out of range.
  */
-#define HG_MAX_TEMPORAL_DEPTH 4
+#define HG_MAX_TEMPORAL_DEPTH 8
 int hg_set_temporal_depth(hg_grid* g, int k);
 
 /* z planes per thread block of the single-sweep kernel (a tuning knob: more blocks and more z warm-up below, fewer

@@ -28,7 +28,7 @@ HG_BC_DIRICHLET_MULTIPOLE = 1
 HG_BC_ROBIN = 2
 HG_BC_PERIODIC = 3
 HG_MAX_LMAX = 8
-HG_MAX_TEMPORAL_DEPTH = 4
+HG_MAX_TEMPORAL_DEPTH = 8
 
 
 class hg_stats(ctypes.Structure):

@@ -10,7 +10,9 @@
 // The x/y neighbours of the plane being updated come from a shared-memory copy of level t-1's middle plane
 // (double-buffered so one barrier per level suffices).  Level t is valid on the region shrunk by t cells on each
 // side, so the 32 - 2K inner columns are written at level K: the K-cell halos are recomputed redundantly by the
-// neighbouring blocks instead of being exchanged.
+// neighbouring blocks instead of being exchanged.  K = 3..8 are built (at K >= 5 the K levels' registers no longer
+// fit the 64 a thread of a 1024-thread block gets, and some spill: deep fusion is there for completeness of the
+// depth sweep, not for speed).
 //
 // Boundary cells inside the region follow the boundary condition at every level: Dirichlet ghosts keep their
 // data, Robin ghosts take the radiation-condition update (the same float-pair formula as the single-sweep ghost
@@ -252,6 +254,10 @@ int launch_temporal(hg_grid* g, int k) {
         case 2: rc = launch_k<2>(g, P, zchunk); break;
         case 3: rc = launch_k<3>(g, P, zchunk); break;
         case 4: rc = launch_k<4>(g, P, zchunk); break;
+        case 5: rc = launch_k<5>(g, P, zchunk); break;
+        case 6: rc = launch_k<6>(g, P, zchunk); break;
+        case 7: rc = launch_k<7>(g, P, zchunk); break;
+        case 8: rc = launch_k<8>(g, P, zchunk); break;
         default: return fail(HG_ERR_ARG, "temporal depth %d not built", k);
     }
     if (rc) return rc;

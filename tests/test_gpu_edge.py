@@ -56,7 +56,7 @@ def test_tiny_and_degenerate_grids_against_oracle(prec, bc, shape):
 
 @pytest.mark.parametrize("shape", SHAPES)
 @pytest.mark.parametrize("bc", ["dirichlet", "robin", "periodic"])
-@pytest.mark.parametrize("depth", [2, 3])
+@pytest.mark.parametrize("depth", [2, 3, 8])
 def test_fused_equals_single_sweeps_on_degenerate_grids(depth, bc, shape):
     nx, ny, nz = shape
     rho, phi0, prev0 = seeded(shape, 711)

@@ -207,6 +207,31 @@ def test_launch_count_and_argument_checks():
         H.set_primitive(np.zeros((5, 8, 8, 7)))
 
 
+def test_mixed_precisions_and_side_stream():
+    """An FP64 hydro state coupled to a compensated-FP32 gravity grid (the density handed over and a read back in
+    the hydro's precision) stays within the FP32 gravity's tolerance of the all-FP64 pair; and a pair created on a
+    side stream gives bit-identical results to the default stream."""
+    n, nsub = 24, 6
+    out = {}
+    for key, prec, stream in (("f64", "f64", None), ("mixed", "f32k", None), ("side", "f64", torch.cuda.Stream())):
+        ctx = torch.cuda.stream(stream) if stream is not None else torch.cuda.stream(torch.cuda.current_stream())
+        with ctx:
+            rho, P, phi, info = I.polytrope(n, pert=0.01, seed=8)
+            W = np.zeros((5, n, n, n))
+            W[0], W[4] = rho, P
+            c, h = 12.0, 1.0 / n
+            dtg = 0.3 * h / (c * np.sqrt(3.0))
+            g = hg.Grid(n, n, n, h, (-0.5, -0.5, -0.5), c, 1.0, dtg, prec, "robin")
+            g.set_phi(torch.from_numpy(phi).cuda())
+            H = hg.Hydro(n, n, n, h, GAMMA, 0.5 * info["rho_atm"], 0.5 * info["p_atm"], dtype="f64")
+            H.set_primitive(torch.from_numpy(W).cuda())
+            for _ in range(3):
+                H.step(nsub * dtg, g, nsub)
+            out[key] = H.state("cpu").numpy()
+    assert np.array_equal(out["side"], out["f64"])
+    assert rel_err(out["mixed"], out["f64"]) < 1e-5
+
+
 @pytest.mark.parametrize("dtype", ["f32", "f64"])
 def test_state_round_trip_host_and_device(dtype):
     shape = (5, 6, 7)

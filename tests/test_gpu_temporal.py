@@ -34,7 +34,7 @@ def make(shape, bc, h=1.0 / 64, depth=1, lmax=0):
 
 @pytest.mark.parametrize("shape", [(61, 45, 37), (96, 31, 70), (30, 30, 30)])
 @pytest.mark.parametrize("bc", ["dirichlet", "multipole", "robin", "periodic"])
-@pytest.mark.parametrize("depth", [2, 3, 4])
+@pytest.mark.parametrize("depth", [2, 3, 4, 5, 6, 7, 8])
 def test_fused_equals_single_sweeps_bitwise(depth, bc, shape):
     rho = I.noise(shape[::-1], 201, 0.0, 2.0)
     phi0 = I.noise(shape[::-1], 202, -1.0, -0.5)
