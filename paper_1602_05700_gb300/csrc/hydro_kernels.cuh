@@ -133,12 +133,13 @@ __device__ __forceinline__ float minmod(float a, float b) {
     return fmaxf(fminf(a, b), fminf(fmaxf(a, b), 0.0f));  // the median of (a, b, 0)
 }
 
-// monotonized-central slope from the one-sided differences a (backward) and b (forward): the argument of least
-// magnitude among 2a, (a + b)/2, 2b when all three have one sign, else 0 -- written as minmod((a + b)/2,
-// 2 minmod(a, b)), which selects the same element (every candidate is computed exactly as in the three-way form)
+// half the monotonized-central slope from the one-sided differences a (backward) and b (forward), i.e. the
+// reconstruction offset to a face: half of the least-magnitude of 2a, (a + b)/2, 2b when all three have one sign,
+// else 0 -- written as minmod((a + b)/4, minmod(a, b)).  Halving is exact, so this selects exactly the value
+// 0.5 * mc(a, b) of the three-way form
 template <typename T>
-__device__ __forceinline__ T mc_slope(T a, T b) {
-    return minmod(T(0.5) * (a + b), T(2) * minmod(a, b));
+__device__ __forceinline__ T mc_half(T a, T b) {
+    return minmod(T(0.25) * (a + b), minmod(a, b));
 }
 
 // conserved state u and physical flux f along axis D of the primitive state w
@@ -199,15 +200,15 @@ __device__ __forceinline__ void flux4(const Gas<T>& G, const T* c0, const T* c1,
 #pragma unroll
     for (int q = 0; q < 5; ++q) {
         const T a = c0[q * PCELLS], b = c1[q * PCELLS], c = c2[q * PCELLS], d = c3[q * PCELLS];
-        wl[q] = b + T(0.5) * mc_slope(b - a, c - b);
-        wr[q] = c - T(0.5) * mc_slope(c - b, d - c);
+        wl[q] = b + mc_half(b - a, c - b);
+        wr[q] = c - mc_half(c - b, d - c);
     }
     hllc<T, D>(G, wl, wr, F);
 }
 
-// z-face between planes k and k+1 of this thread's column: the limited slope of plane k (carried from the
-// previous plane, where it was the upper cell's slope) and that of plane k+1 (computed here from planes k, k+1,
-// k+2 and carried on); the same operations on the same values as flux4, each slope evaluated once
+// z-face between planes k and k+1 of this thread's column: the limited half-slope of plane k (carried from the
+// previous plane, where it was the upper cell's) and that of plane k+1 (computed here from planes k, k+1, k+2 and
+// carried on); the same operations on the same values as flux4, each slope evaluated once
 template <typename T>
 __device__ __forceinline__ void zflux(const Gas<T>& G, const T* ck, const T* ck1, const T* ck2, const T sk[5],
                                       T sk1[5], T F[5]) {
@@ -215,20 +216,20 @@ __device__ __forceinline__ void zflux(const Gas<T>& G, const T* ck, const T* ck1
 #pragma unroll
     for (int q = 0; q < 5; ++q) {
         const T b = ck[q * PCELLS], c = ck1[q * PCELLS], d = ck2[q * PCELLS];
-        sk1[q] = mc_slope(c - b, d - c);
-        wl[q] = b + T(0.5) * sk[q];
-        wr[q] = c - T(0.5) * sk1[q];
+        sk1[q] = mc_half(c - b, d - c);
+        wl[q] = b + sk[q];
+        wr[q] = c - sk1[q];
     }
     hllc<T, 2>(G, wl, wr, F);
 }
 
-// limited slope of this thread's cell in plane p from planes p-1, p, p+1
+// limited half-slope of this thread's cell in plane p from planes p-1, p, p+1
 template <typename T>
 __device__ __forceinline__ void zslope(const T* cm, const T* c0, const T* cp, T s[5]) {
 #pragma unroll
     for (int q = 0; q < 5; ++q) {
         const T a = cm[q * PCELLS], b = c0[q * PCELLS], c = cp[q * PCELLS];
-        s[q] = mc_slope(b - a, c - b);
+        s[q] = mc_half(b - a, c - b);
     }
 }
 
