@@ -718,22 +718,24 @@ def run_virial(args):
     from paper_1602_05700_gb300 import inputs as I
 
     n, steps, cfl = args.n, args.substeps, 0.3
+    f64 = args.prec == "f64"  # FP64 hydro and gravity (the oracle-exact mode) instead of FP32 / compensated FP32
     h = 1.0 / n
     t_dyn = (1.0 / 3.0) ** 1.5  # sqrt(R^3 / (G M))
     res = {"workload": f"{n}^3 n=3 polytrope (M 1, R 1/3), gamma 5/3, Robin gravity, Courant {cfl:g}, "
-                       f"{steps} hydro steps", "t_dyn": t_dyn}
+                       f"{steps} hydro steps, {'FP64' if f64 else 'FP32 hydro + compensated FP32 gravity'}",
+           "t_dyn": t_dyn}
     ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
     for label, pert, kg in (("unperturbed", 0.0, 5.0), ("perturbed_1pct", 0.01, 5.0), ("unperturbed_kg20", 0.0, 20.0)):
         rho, P, phi, info = I.polytrope(n, pert=pert, seed=21)
-        W = np.zeros((5, n, n, n), np.float32)
+        W = np.zeros((5, n, n, n), np.float64 if f64 else np.float32)
         W[0], W[4] = rho, P
-        H = hg.Hydro(n, n, n, h, 5.0 / 3.0, 0.5 * info["rho_atm"], 0.5 * info["p_atm"], dtype="f32")
+        H = hg.Hydro(n, n, n, h, 5.0 / 3.0, 0.5 * info["rho_atm"], 0.5 * info["p_atm"], dtype="f64" if f64 else "f32")
         H.set_primitive(torch.from_numpy(W).cuda())
         del W
         s0 = H.max_speed()
         c = kg * s0
         dtg = cfl * h / (c * np.sqrt(3.0))
-        g = hg.Grid(n, n, n, h, (-0.5, -0.5, -0.5), c, 1.0, dtg, "f32k", "robin")
+        g = hg.Grid(n, n, n, h, (-0.5, -0.5, -0.5), c, 1.0, dtg, "f64" if f64 else "f32k", "robin")
         g.set_phi(torch.from_numpy(phi).cuda())
         v0 = H.virial(g)
         trace = [(0.0, v0["VC"], 1.0)]
@@ -787,13 +789,15 @@ def run_virial(args):
             ms_hyd = timed(lambda: H.step(dt))
             pk, kind = peaks()
             t_stage = res[label]["stage_kernel_ms_avg"] * 1e-3  # event-timed stage launches of the evolution
-            alg = 62 * n ** 3  # bytes per stage launch with gravity: avg of (8 read + 5 write) and (13 + 5) floats
-            winst = kernel_instructions("k_hydro_stage<float>", n ** 3)
+            alg = (124 if f64 else 62) * n ** 3  # bytes per stage launch with gravity: avg of (8 read + 5 write)
+            #                                      and (13 + 5) values
+            winst = None if f64 else kernel_instructions("k_hydro_stage<float>", n ** 3)
             res["timing"] = {"ms_per_coupled_step": round(ms_step, 4), "ms_gravity_substeps_and_accel": round(ms_grav, 4),
                              "ms_hydro_two_stages_without_gravity": round(ms_hyd, 4),
                              "gcell_hydro_steps_per_s": round(n ** 3 / (ms_step * 1e-3) / 1e9, 3),
                              "hydro_stage_roofline": {
-                                 "bound": "alu", "kernel": "k_hydro_stage<float>", "unit": "G warp-instr/s",
+                                 "bound": "alu", "kernel": "k_hydro_stage<double>" if f64 else "k_hydro_stage<float>",
+                                 "unit": "G warp-instr/s",
                                  "achieved": round(winst / t_stage / 1e9, 1) if winst else None,
                                  "peak": round(ISSUE_PEAK_GWIPS, 1),
                                  "frac": round(winst / t_stage / 1e9 / ISSUE_PEAK_GWIPS, 4) if winst else None,
@@ -803,7 +807,7 @@ def run_virial(args):
                                  "hbm_achieved_gbs": round(alg / t_stage / 1e9, 1),
                                  "hbm_frac": round(alg / t_stage / 1e9 / pk, 4), "hbm_peak_kind": kind,
                                  "alg_bytes_per_launch": alg,
-                                 "traffic": stencil_traffic("k_hydro_stage<float>", n)}}
+                                 "traffic": None if f64 else stencil_traffic("k_hydro_stage<float>", n)}}
         g.free()
         H.free()
     return res
