@@ -179,6 +179,12 @@ int hg_adjoint_reset(hg_grid* g);
 int hg_adjoint_inject(hg_grid* g, const void* dL_dphi, int dtype, int on_device);
 int hg_adjoint_step(hg_grid* g, int n_substeps);
 int hg_adjoint_grad(hg_grid* g, void* dL_drho, int dtype, int on_device);
+/* The whole terminal-loss case in one call: dL_drho = dL/drho for L = L(phi^T) after T forward sub-steps, given
+ * dL_dphiT = dL/dphi^T (both nz*ny*nx values of element type dtype, on the device if on_device); the same as reset,
+ * inject, step(T), grad.  No checkpoint interval is taken: the reverse recursion of the linear sub-step needs no
+ * forward state (checkpointing matters for losses on intermediate potentials and is done by the Python binding's
+ * autograd.trajectory_loss).  HG_ERR_ARG for T < 0 or null pointers. */
+int hg_adjoint(hg_grid* g, const void* dL_dphiT, int T, void* dL_drho, int dtype, int on_device);
 
 /*
  * Measurement hooks.  hg_profile(g, 1) makes the library record a pair of CUDA events on the grid's stream around

@@ -282,6 +282,16 @@ class Grid:
         _lib.check(_lib.lib().hg_adjoint_grad(self.handle, ctypes.c_void_p(out.data_ptr()), code, 1))
         return out
 
+    def adjoint(self, dL_dphiT, T):
+        """dL/drho for L = L(phi^T) after T sub-steps, given dL/dphi^T, in one call (hg_adjoint)."""
+        torch = _torch()
+        p, code, dev, keep = _buffer(dL_dphiT)
+        self._check_size(keep)
+        out = torch.empty(self.shape, dtype=torch.float64 if code == HG_DT_F64 else torch.float32,
+                          device=self.device if dev else "cpu")
+        _lib.check(_lib.lib().hg_adjoint(self.handle, p, int(T), ctypes.c_void_p(out.data_ptr()), code, dev))
+        return out
+
     def profile(self, enable=True):
         _lib.check(_lib.lib().hg_profile(self.handle, 1 if enable else 0))
 

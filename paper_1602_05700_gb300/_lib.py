@@ -69,6 +69,7 @@ SIGNATURES = {
     "hg_adjoint_inject": (_I, [_V, _V, _I, _I]),
     "hg_adjoint_step": (_I, [_V, _I]),
     "hg_adjoint_grad": (_I, [_V, _V, _I, _I]),
+    "hg_adjoint": (_I, [_V, _V, _I, _V, _I, _I]),
     "hg_profile": (_I, [_V, _I]),
     "hg_profile_read": (_I, [_V, _P(_D), _P(ctypes.c_longlong), _P(ctypes.c_longlong)]),
     "hg_io_step": (_I, [_V, _V, _I, _I, _V, _V, _V, _I]),

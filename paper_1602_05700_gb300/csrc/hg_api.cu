@@ -681,6 +681,17 @@ static int io_ready(hg_grid* g, size_t rho_bytes, size_t acc_bytes) {
     return HG_OK;
 }
 
+int hg_adjoint(hg_grid* g, const void* dL_dphiT, int T, void* dL_drho, int dtype, int on_device) {
+    int rc = check_grid(g);
+    if (rc) return rc;
+    if (!dL_dphiT || !dL_drho) return fail(HG_ERR_ARG, "null adjoint buffer");
+    if (T < 0) return fail(HG_ERR_ARG, "T must be >= 0");
+    if ((rc = hg_adjoint_reset(g))) return rc;
+    if ((rc = hg_adjoint_inject(g, dL_dphiT, dtype, on_device))) return rc;
+    if ((rc = hg_adjoint_step(g, T))) return rc;
+    return hg_adjoint_grad(g, dL_drho, dtype, on_device);
+}
+
 int hg_io_step(hg_grid* g, const void* rho_host, int rho_dtype, int n_substeps, void* ax_host, void* ay_host,
                void* az_host, int acc_dtype) {
     int rc = check_grid(g);

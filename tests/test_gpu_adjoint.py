@@ -37,6 +37,9 @@ def test_adjoint_matches_oracle(prec, bc):
     g.adjoint_inject(lam)  # from host memory this time
     g.adjoint_step(T)
     assert np.array_equal(g.adjoint_grad().cpu().numpy(), got)
+    # the one-call terminal-loss form gives the same result, from device and from host buffers
+    assert np.array_equal(g.adjoint(torch.from_numpy(lam).cuda(), T).cpu().numpy(), got)
+    assert np.array_equal(g.adjoint(lam, T).numpy(), got)
 
 
 def _probe_loss(grid, T, probes, target):
