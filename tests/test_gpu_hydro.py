@@ -87,6 +87,31 @@ def test_fp64_floors_bit_exact():
     assert U[0].min() >= 1e-3
 
 
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_strong_blast(dtype):
+    """A point-like blast (pressure ratio 1e5): FP64 bit-exact with the oracle; FP32 finite, positive, and mass and
+    energy conserved to its rounding while the shock is inside the box."""
+    shape = (40, 36, 44)
+    H, hgo = pair(shape, dtype, gamma=1.4)
+    W = np.zeros((5,) + shape)
+    W[0], W[4] = 1.0, 1e-5
+    W[4, 19:21, 17:19, 21:23] = 1.0
+    H.set_primitive(W)
+    U = O.hydro_cons(hgo, W)
+    tot0 = U.reshape(5, -1).sum(axis=1)
+    for _ in range(15):
+        dt = 0.3 * hgo.h / O.hydro_max_speed(hgo, U)
+        H.step(dt)
+        O.hydro_step(hgo, U, dt)
+    got = H.state("cpu").numpy().astype(np.float64)
+    if dtype == "f64":
+        assert np.array_equal(got, U)
+    else:
+        assert np.isfinite(got).all() and got[0].min() > 0
+        tot = got.reshape(5, -1).sum(axis=1)
+        assert abs(tot[0] - tot0[0]) < 1e-5 * tot0[0] and abs(tot[4] - tot0[4]) < 1e-4 * tot0[4]
+
+
 @pytest.mark.parametrize("shape", [(23, 19, 37), (1, 1, 1), (1, 1, 64), (40, 1, 1), (1, 33, 1), (3, 2, 33),
                                    (17, 9, 100)])
 def test_fp32_hydro_steps_within_tolerance(shape):

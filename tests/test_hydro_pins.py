@@ -8,6 +8,7 @@ as the source -rho grad phi) and of the polytrope input, against what mathematic
   to rounding (an HLL flux would smear it)                            -> the star states and the contact speed
 * smooth advection converges at second order (error ratio > 3.5 per halving) -> limiter, two-stage integrator
 * conservation of mass, momentum and energy to rounding                -> flux differencing, boundary
+* a strong blast stays positive and conservative                       -> robustness of the limiter and solver
 * uniform field on a uniform gas: exact Heun response m = rho a dt, E - E0 = rho |a|^2 dt^2 / 2 -> source terms
 * characteristic speed of a hand-computed state                       -> the c_g normalisation
 * Lane-Emden closed forms (n = 0, 1, 5) and textbook constants (n = 1.5, 3) -> the polytrope input
@@ -199,6 +200,25 @@ def test_conservation_to_rounding():
     scale = np.abs(U).reshape(5, -1).sum(axis=1)
     assert np.all(np.abs(tot - tot0) <= 1e-14 * scale), (tot - tot0) / scale
     assert np.abs(U[:, :2] - O.hydro_cons(hg, W)[:, :2]).max() == 0.0
+
+
+def test_strong_blast_stays_positive_and_conservative():
+    """A point-like blast (pressure ratio 1e5) in a box of gas at rest: no floor needed, density and pressure stay
+    positive, mass and energy are conserved to rounding while the shock is inside the box."""
+    n = 24
+    hg = O.HydroGrid(n, n, n, 1.0 / n, 1.4)
+    W = np.zeros((5, n, n, n))
+    W[0], W[4] = 1.0, 1e-5
+    W[4, 11:13, 11:13, 11:13] = 1.0
+    U = O.hydro_cons(hg, W)
+    tot0 = U.reshape(5, -1).sum(axis=1)
+    for _ in range(12):
+        O.hydro_step(hg, U, 0.3 * hg.h / O.hydro_max_speed(hg, U))
+    Wf = O.hydro_prim(hg, U)
+    assert np.isfinite(U).all() and Wf[0].min() > 0 and Wf[4].min() > 0
+    assert np.abs(U[:, :2] - O.hydro_cons(hg, W)[:, :2]).max() == 0.0  # the shock has not reached the faces
+    tot = U.reshape(5, -1).sum(axis=1)
+    assert abs(tot[0] - tot0[0]) <= 1e-14 * tot0[0] and abs(tot[4] - tot0[4]) <= 1e-13 * tot0[4]
 
 
 def test_uniform_field_source_is_exact_heun():
