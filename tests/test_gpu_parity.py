@@ -114,6 +114,37 @@ def test_sphere_dirichlet_analytic_32(prec):
     assert abs(st["residual_max"] - mx) < (1e-9 if prec == "f64" else 1e-3) * mx
 
 
+def test_sphere_robin_run_to_convergence_24():
+    """Config 1 with the absorbing boundary, run to convergence on the GPU (the paper's stopping rule: relative change
+    per sub-step below 1e-10): the converged FP64 potential is the discrete Robin-Poisson fixed point (sparse direct
+    solve) and the analytic sphere within its discretisation error; the compensated-FP32 grid run for the same
+    number of sub-steps lands on the same fixed point within its tolerance."""
+    from tests import poisson_ref as R
+    n = 24
+    rho = I.sphere_density(n)
+    og = O.unit_cube(n, 1.0, 1.0, 0.5, O.BC_ROBIN)
+    fixed = R.robin_poisson(og.h, og.G, og.origin, rho)
+    X, Y, Z = og.centres()
+    an = R.analytic_sphere(X, Y, Z)
+    g = hg.Grid.unit_cube(n, 1.0, 1.0, 0.5, "f64", "robin")
+    g.set_density(rho)
+    steps = 0
+    while steps < 100000:
+        g.step(500)
+        steps += 500
+        if g.stats()["change_rel"] < 1e-10:
+            break
+    assert g.stats()["change_rel"] < 1e-10, steps
+    u = g.phi(torch.float64, "cpu")
+    assert np.abs(u - fixed).max() < 1e-6 * np.abs(fixed).max(), (steps, np.abs(u - fixed).max())
+    assert np.sqrt(np.mean((u - an) ** 2) / np.mean(an ** 2)) < 5e-3
+    g32 = hg.Grid.unit_cube(n, 1.0, 1.0, 0.5, "f32k", "robin")
+    g32.set_density(rho)
+    g32.step(steps)
+    u32 = g32.phi(torch.float64, "cpu")
+    assert np.abs(u32 - fixed).max() < 1e-5 * np.abs(fixed).max()
+
+
 @pytest.mark.parametrize("prec", ["f64", "f32k"])
 def test_precision_config_2000_substeps(prec):
     """Config-2 workload at 64^3 (the oracle's size): sphere + 8 blobs (seed 1), multipole l <= 4, 2000 sub-steps."""
