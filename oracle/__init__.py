@@ -71,6 +71,8 @@ def _L():
         d = ctypes.c_double
         dp = P(d)
         gp = P(_OgGrid)
+        lib.og_exact_sum.restype = d
+        lib.og_exact_sum.argtypes = [dp, ctypes.c_size_t]
         lib.og_mean.restype = d
         lib.og_mean.argtypes = [gp, dp]
         lib.og_mass.restype = d
@@ -156,6 +158,13 @@ def ghosted(g: Grid, interior: np.ndarray | None = None) -> np.ndarray:
 
 def interior(a: np.ndarray) -> np.ndarray:
     return np.ascontiguousarray(a[1:-1, 1:-1, 1:-1])
+
+
+def exact_sum(x: np.ndarray) -> float:
+    """The sum of the values rounded once to the nearest double (the oracle's summation of every sum the method
+    defines: moments, mass, mean)."""
+    x = np.ascontiguousarray(x, dtype=np.float64).ravel()
+    return _L().og_exact_sum(_p(x), x.size)
 
 
 def mean(g: Grid, rho: np.ndarray) -> float:

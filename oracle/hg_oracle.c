@@ -65,19 +65,77 @@ static size_t nghosted(const og_grid* g) { return (size_t)(g->nx + 2) * (g->ny +
 static double og_nu(const og_grid* g) { return g->c * g->dt / g->h; }
 static double og_src(const og_grid* g) { return (g->c * g->dt) * (g->c * g->dt) * 4.0 * OG_PI * g->G; }
 
-double og_mean(const og_grid* g, const double* rho) {
-    double s = 0.0;
-    size_t n = ncells(g);
-    for (size_t q = 0; q < n; ++q) s += rho[q];
-    return s / (double)n;
+/* ---- sums -----------------------------------------------------------------------------------------------
+ * Reading: a sum the method defines (the multipole moments Q_lm of Sec. 4, the mass, the mean density subtracted
+ * from the source with periodic boundaries, Sec. 4) is the exact sum of its terms, rounded once to the nearest
+ * double.  That value does not depend on the order of the terms.  A plain running sum of the 1.7e7 cells of a
+ * 256^3 grid instead carries a rounding error of order 1e-12 relative, and the lossless scheme carries every bit
+ * of the Dirichlet data into phi.
+ * The exact sum is held as a nonoverlapping expansion (Shewchuk 1997, "Adaptive precision floating-point
+ * arithmetic and fast robust geometric predicates", Grow-Expansion with zero elimination): components in
+ * increasing magnitude whose exact sum is the sum of all terms so far; a new term passes through every component
+ * by an error-free two-sum, keeping the nonzero rounding errors.  A double expansion has at most a few dozen
+ * nonzero components. */
+#define OG_XMAX 80
+typedef struct {
+    int n;
+    double p[OG_XMAX];
+} og_xsum;
+
+static void xsum_init(og_xsum* s) { s->n = 0; }
+
+static void xsum_add(og_xsum* s, double x) {
+    int kept = 0;
+    for (int c = 0; c < s->n; ++c) {
+        double y = s->p[c];
+        double big = fabs(x) >= fabs(y) ? x : y, small = fabs(x) >= fabs(y) ? y : x;
+        double t = big + small;
+        double err = small - (t - big); /* exact: t + err = x + y */
+        if (err != 0.0) s->p[kept++] = err;
+        x = t;
+    }
+    s->p[kept++] = x;
+    s->n = kept;
 }
+
+/* The expansion's exact value rounded to the nearest double (ties to even).  Walking down from the largest
+ * component, t is the rounded sum of the components seen so far and err its exact rounding error; the first
+ * nonzero err ends the walk, since every component left is smaller than half an ulp of t.  Those components only
+ * matter when err is exactly half an ulp (a tie that the addition broke to even): if they push the same way as
+ * err, the exact value lies beyond the midpoint and rounds to t + 2 err. */
+static double xsum_value(const og_xsum* s) {
+    if (s->n == 0) return 0.0;
+    int c = s->n - 1;
+    double t = s->p[c], err = 0.0;
+    while (c > 0) {
+        double y = s->p[--c];
+        double u = t + y;
+        err = y - (u - t);
+        t = u;
+        if (err != 0.0) break;
+    }
+    if (c > 0 && err != 0.0 && ((err > 0.0) == (s->p[c - 1] > 0.0)) && s->p[c - 1] != 0.0) {
+        double twice = 2.0 * err;
+        double v = t + twice;
+        if (v - t == twice) t = v; /* err was exactly half an ulp of t */
+    }
+    return t;
+}
+
+/* exported for the tests: the correctly rounded sum of n doubles */
+double og_exact_sum(const double* x, size_t n) {
+    og_xsum s;
+    xsum_init(&s);
+    for (size_t q = 0; q < n; ++q) xsum_add(&s, x[q]);
+    return xsum_value(&s);
+}
+
+/* mean density (periodic boundaries subtract it from the source, Sec. 4) */
+double og_mean(const og_grid* g, const double* rho) { return og_exact_sum(rho, ncells(g)) / (double)ncells(g); }
 
 /* total mass sum rho h^3 */
 double og_mass(const og_grid* g, const double* rho) {
-    double s = 0.0;
-    size_t n = ncells(g);
-    for (size_t q = 0; q < n; ++q) s += rho[q];
-    return s * g->h * g->h * g->h;
+    return og_exact_sum(rho, ncells(g)) * g->h * g->h * g->h;
 }
 
 /* ---- face iteration: face f in 0..5 = (-x, +x, -y, +y, -z, +z) ------------------------------------------- */
@@ -141,13 +199,15 @@ static void real_ylm(int lmax, double x, double y, double z, double* Y) {
 void og_real_ylm(int lmax, double x, double y, double z, double* Y) { real_ylm(lmax, x, y, z, Y); }
 
 /* Multipole moments Q_lm = sum_j rho_j h^3 r_j^l Y_lm(x_j / r_j) about the coordinate origin (Sec. 4, Dirichlet
- * boundary by multipole expansion).  Q has (lmax+1)^2 entries.  A cell centred exactly at the origin adds only to
+ * boundary by multipole expansion), each the exact sum of its terms rounded once (see "sums" above).  Q has
+ * (lmax+1)^2 entries.  A cell centred exactly at the origin adds only to
  * Q_00 (r^l Y_lm vanishes there for l > 0). */
 void og_moments(const og_grid* g, const double* rho, int lmax, double* Q) {
     int nq = (lmax + 1) * (lmax + 1);
     double Y[32 * 32];
     double h3 = g->h * g->h * g->h;
-    for (int q = 0; q < nq; ++q) Q[q] = 0.0;
+    og_xsum* acc = (og_xsum*)malloc((size_t)nq * sizeof(og_xsum));
+    for (int q = 0; q < nq; ++q) xsum_init(&acc[q]);
     for (int k = 0; k < g->nz; ++k)
         for (int j = 0; j < g->ny; ++j)
             for (int i = 0; i < g->nx; ++i) {
@@ -155,16 +215,18 @@ void og_moments(const og_grid* g, const double* rho, int lmax, double* Q) {
                 double x = cx(g, i), y = cy(g, j), z = cz(g, k);
                 double r = sqrt(x * x + y * y + z * z);
                 if (r == 0.0) {
-                    Q[0] += m / sqrt(4.0 * OG_PI);
+                    xsum_add(&acc[0], m / sqrt(4.0 * OG_PI));
                     continue;
                 }
                 real_ylm(lmax, x, y, z, Y);
                 double rl = 1.0;
                 for (int l = 0; l <= lmax; ++l) {
-                    for (int mm = -l; mm <= l; ++mm) Q[l * l + l + mm] += m * rl * Y[l * l + l + mm];
+                    for (int mm = -l; mm <= l; ++mm) xsum_add(&acc[l * l + l + mm], m * rl * Y[l * l + l + mm]);
                     rl *= r;
                 }
             }
+    for (int q = 0; q < nq; ++q) Q[q] = xsum_value(&acc[q]);
+    free(acc);
 }
 
 /* Exterior multipole potential at (x,y,z): -G sum_l 4 pi/(2l+1) r^{-(l+1)} sum_m Q_lm Y_lm. */

@@ -410,3 +410,40 @@ def test_dirichlet_poisson_reference_of_the_domain_study():
         e = exact[1:-1, 1:-1, 1:-1]
         errs.append(np.linalg.norm(phi - e) / np.linalg.norm(e))
     assert errs[1] < 2e-3 and errs[0] / errs[1] > 3.5
+
+
+def test_exact_sum_is_the_correctly_rounded_sum():
+    """The oracle's sums (moments, mass, mean) are the exact sum rounded once; pinned bit for bit against the
+    library routine math.fsum (which returns exactly that) on inputs where a running sum goes wrong: massive
+    cancellation, a dynamic range beyond 2^1000, exact ties between two doubles (rounded to even, and pushed off
+    the tie by a tiny remainder of either sign), and long random sums with a known exact cancellation."""
+    import math
+
+    rng = np.random.default_rng(11)
+    cases = [
+        [],
+        [0.0, -0.0],
+        [1.0, 1e100, 1.0, -1e100],
+        [1e300, 1e300, -1e300, -1e300, 1e-300],
+        [1.0, 2.0 ** -53],                      # tie, 1 is even: stays 1
+        [1.0 + 2.0 ** -52, 2.0 ** -53],        # tie, rounds up to the even neighbour
+        [1.0, 2.0 ** -53, 2.0 ** -200],        # just above the tie: rounds up
+        [1.0 + 2.0 ** -52, 2.0 ** -53, -2.0 ** -200],  # just below the tie: rounds down
+        [1.0, -2.0 ** -54, -2.0 ** -300],
+        [2.0 ** 53, 1.0, 2.0 ** -60, -(2.0 ** 53)],
+        [float(v) for v in rng.standard_normal(10000) * 10.0 ** rng.integers(-30, 30, 10000)],
+    ]
+    big = rng.standard_normal(200000) * 10.0 ** rng.integers(-8, 8, 200000)
+    cases.append(list(np.concatenate([big, -big[::-1], [3.5e-17]])))
+    cases.append(list(rng.random(100000)))
+    for c in cases:
+        got = O.exact_sum(np.array(c, dtype=np.float64))
+        want = math.fsum(c)
+        assert got == want or (got == 0.0 and want == 0.0), (got, want)
+    # the running sum of the same random cancellation case is far off; the exact one is not
+    a = np.concatenate([big, -big[::-1], [3.5e-17]])
+    assert O.exact_sum(a) == 3.5e-17
+    g = O.unit_cube(8, 1.0, 1.0, 0.5, O.BC_PERIODIC)
+    rho = rng.random((8, 8, 8))
+    assert O.mass(g, rho) == math.fsum(rho.ravel()) * g.h * g.h * g.h
+    assert O.mean(g, rho) == math.fsum(rho.ravel()) / rho.size
