@@ -155,7 +155,9 @@ int hg_compare(hg_grid* g, const double* phi_P, int on_device, double out[3]);
 
 /* Checkpoint / resume of the full state (bit-exact): hg_state_bytes gives the size of the opaque buffer that
  * hg_save_state fills and hg_load_state reads, in host memory (on_device = 0) or device memory (on_device = 1).
- * A buffer is only valid for a grid of the same sizes, precision and boundary condition. */
+ * A buffer is only valid for a grid of the same sizes, precision, boundary condition and lmax, and with
+ * bit-identical h, origin, c_h, G and dt (the stored source, the Dirichlet data and the Robin coefficients depend on
+ * them); hg_load_state returns HG_ERR_ARG, and changes nothing, for any other buffer. */
 size_t hg_state_bytes(const hg_grid* g);
 int hg_save_state(hg_grid* g, void* buf, int on_device);
 int hg_load_state(hg_grid* g, const void* buf, int on_device);
@@ -265,11 +267,12 @@ void hg_batch_free(hg_batch* b);
  * (Q_on_device = 0: the call then synchronises the stream); same definition and index as hg_get_moments.
  * cuda_stream: the stream the work is enqueued on (NULL = legacy default stream), on the current device.
  *
- * Scratch: a fixed array compiled into the library, 304 x 81 + 81 doubles (197,640 bytes), present on every GPU
+ * Scratch: a fixed array compiled into the library, 2 x 152 x 81 + 81 doubles (197,640 bytes), present on every GPU
  * that loads the library until the process exits.  Its size is what bounds lmax: lmax > HG_MAX_LMAX is rejected
  * with HG_ERR_ARG; grid sizes are not limited by it.  The first call on each device looks up the array's device
  * address (cudaGetSymbolAddress) with that device current and caches it; make that first call before any stream
- * capture.  All calls on a device share the one array: every call overwrites the partial sums it uses, so no
+ * capture.  The cache is keyed by the device and its CUDA context, so after a cudaDeviceReset the next call looks
+ * the address up again (in the new context) instead of using the old one.  All calls on a device share the one array: every call overwrites the partial sums it uses, so no
  * state carries over from the previous call, but calls whose GPU work overlaps in time (other streams, other host
  * threads) race on the array and must be serialised by the caller.
  * Errors: HG_ERR_ARG (null pointer, bad dtype, sizes < 1, h <= 0, lmax out of range), HG_ERR_CUDA.

@@ -79,44 +79,97 @@ __device__ __forceinline__ double load_as_double(const void* p, int dtype, long 
 }
 
 
+// ---- double-double sums of the moments -----------------------------------------------------------------------
+// Each moment is a sum over every cell (1.7e7 terms at 256^3).  A plain running or tree sum in FP64 carries a
+// rounding error that the lossless scheme then carries, through the Dirichlet data, into phi; so every partial sum
+// is kept as an unevaluated pair s + e (TwoSum: s is the rounded sum, e collects the exact rounding errors), whose
+// error is of order n eps^2 of the sum of |terms|.  The final s + e, rounded once, is then the correctly rounded
+// sum of the terms except in the rare case that the exact sum lies within that tiny error of a midpoint between
+// two doubles.
+__device__ __forceinline__ void dd_add(double& s, double& e, double x) {
+    const double t = __dadd_rn(s, x);
+    const double v = __dsub_rn(t, s);
+    e = __dadd_rn(e, __dadd_rn(__dsub_rn(s, __dsub_rn(t, v)), __dsub_rn(x, v)));
+    s = t;
+}
+// (s, e) += (s2, e2), renormalised so that s is the rounded value of the pair
+__device__ __forceinline__ void dd_merge(double& s, double& e, double s2, double e2) {
+    dd_add(s, e, s2);
+    e = __dadd_rn(e, e2);
+    const double t = __dadd_rn(s, e);
+    e = __dsub_rn(e, __dsub_rn(t, s));
+    s = t;
+}
+__device__ __forceinline__ void dd_warp(double& s, double& e) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const double s2 = __shfl_xor_sync(0xffffffffu, s, o), e2 = __shfl_xor_sync(0xffffffffu, e, o);
+        dd_merge(s, e, s2, e2);
+    }
+}
+// block sum of one pair per thread (blockDim.x a multiple of 32, at most 1024); result valid in thread 0
+__device__ __forceinline__ void dd_block(double& s, double& e, double* sh) {
+    dd_warp(s, e);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) {
+        sh[2 * w] = s;
+        sh[2 * w + 1] = e;
+    }
+    __syncthreads();
+    if (w == 0) {
+        const bool have = l < (int)(blockDim.x >> 5);
+        s = have ? sh[2 * l] : 0.0;
+        e = have ? sh[2 * l + 1] : 0.0;
+        dd_warp(s, e);
+    }
+}
+
+constexpr int kMomBlocks = 152;  // fixed, so that the result does not depend on the device
+
 template <int LMAX>
 __global__ void __launch_bounds__(kRedThreads) k_moments(const void* rho, int dtype, int nx, int ny, int nz, double h,
                                                          double ox, double oy, double oz, YlmNorm N,
                                                          double* partial) {
     constexpr int NQ = (LMAX + 1) * (LMAX + 1);
-    __shared__ double sh[32];
-    double acc[NQ];
+    __shared__ double sh[64];
+    double as[NQ], ae[NQ];
 #pragma unroll
-    for (int q = 0; q < NQ; ++q) acc[q] = 0.0;
+    for (int q = 0; q < NQ; ++q) as[q] = ae[q] = 0.0;
     const long long n = (long long)nx * ny * nz;
-    const double h3 = h * h * h;
+    const double h3 = __dmul_rn(__dmul_rn(h, h), h);
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
         const int i = (int)(c % nx);
         const long long r = c / nx;
         const int j = (int)(r % ny);
         const int k = (int)(r / ny);
-        const double m = load_as_double(rho, dtype, c) * h3;
+        const double m = __dmul_rn(load_as_double(rho, dtype, c), h3);
         if (m == 0.0) continue;
         double R[NQ];
         solid_harmonics<LMAX>(ox + (i + 0.5) * h, oy + (j + 0.5) * h, oz + (k + 0.5) * h, N, R);
 #pragma unroll
-        for (int q = 0; q < NQ; ++q) acc[q] = fma(m, R[q], acc[q]);
+        for (int q = 0; q < NQ; ++q) dd_add(as[q], ae[q], __dmul_rn(m, R[q]));
     }
 #pragma unroll
     for (int q = 0; q < NQ; ++q) {
-        double s = block_sum(acc[q], sh);
-        if (threadIdx.x == 0) partial[(long long)blockIdx.x * NQ + q] = s;
+        double s = as[q], e = ae[q];
+        dd_block(s, e, sh);
+        if (threadIdx.x == 0) {
+            partial[2 * ((long long)blockIdx.x * NQ + q)] = s;
+            partial[2 * ((long long)blockIdx.x * NQ + q) + 1] = e;
+        }
     }
 }
 
-// sum partial[b * nq + q] over b in a fixed order (one block)
+// sum the pairs partial[2 (b nq + q) + {0, 1}] over b in a fixed order (one block); out[q] = the rounded pair
 __global__ void __launch_bounds__(kRedThreads) k_finish(const double* partial, int nblocks, int nq, double* out) {
-    __shared__ double sh[32];
+    __shared__ double sh[64];
     for (int q = 0; q < nq; ++q) {
-        double v = 0.0;
-        for (int b = threadIdx.x; b < nblocks; b += blockDim.x) v += partial[(long long)b * nq + q];
-        v = block_sum(v, sh);
-        if (threadIdx.x == 0) out[q] = v;
+        double s = 0.0, e = 0.0;
+        for (int b = threadIdx.x; b < nblocks; b += blockDim.x)
+            dd_merge(s, e, partial[2 * ((long long)b * nq + q)], partial[2 * ((long long)b * nq + q) + 1]);
+        dd_block(s, e, sh);
+        if (threadIdx.x == 0) out[q] = s;
     }
 }
 
@@ -223,10 +276,10 @@ __global__ void k_periodic(int prec, void* p, void* lo, Layout L, Faces F) {
 template <int LMAX>
 int run_moments(hg_grid* g, const void* rho, int dtype) {
     constexpr int NQ = (LMAX + 1) * (LMAX + 1);
-    k_moments<LMAX><<<kRedBlocks, kRedThreads, 0, g->stream>>>(rho, dtype, g->nx, g->ny, g->nz, g->h, g->origin[0],
+    k_moments<LMAX><<<kMomBlocks, kRedThreads, 0, g->stream>>>(rho, dtype, g->nx, g->ny, g->nz, g->h, g->origin[0],
                                                                 g->origin[1], g->origin[2], g->ylm, g->red);
     HG_LAUNCHED("multipole moment kernel");
-    k_finish<<<1, kRedThreads, 0, g->stream>>>(g->red, kRedBlocks, NQ, g->dres);
+    k_finish<<<1, kRedThreads, 0, g->stream>>>(g->red, kMomBlocks, NQ, g->dres);
     HG_LAUNCHED("moment finish kernel");
     return HG_OK;
 }
@@ -246,7 +299,10 @@ int run_dirichlet(hg_grid* g) {
 
 }  // namespace
 
-long long reduction_scratch_elems() { return (long long)kRedBlocks * kMaxQ; }
+long long reduction_scratch_elems() {
+    const long long a = (long long)kRedBlocks * kMaxQ, b = 2LL * kMomBlocks * kMaxQ;
+    return a > b ? a : b;
+}
 
 int compute_moments(hg_grid* g, const void* rho_dense, int dtype) {
     int rc;
@@ -323,28 +379,62 @@ int seed_ghosts(hg_grid* g) {
 namespace hg {
 namespace {
 
-// partial sums of kRedBlocks blocks for up to kMaxQ moments, then kMaxQ doubles for a result bound for host memory:
-// (304 * 81 + 81) doubles = 197,640 bytes on every GPU that loads the library, held until the process exits
-constexpr int kNoAllocDoubles = kRedBlocks * kMaxQ + kMaxQ;
+// partial sums (pairs) of kMomBlocks blocks for up to kMaxQ moments, then kMaxQ doubles for a result bound for host
+// memory: (2 * 152 * 81 + 81) doubles = 197,640 bytes on every GPU that loads the library, held until the process
+// exits
+constexpr int kNoAllocDoubles = 2 * kMomBlocks * kMaxQ + kMaxQ;
 static __device__ __align__(256) double g_noalloc_scratch[kNoAllocDoubles];
 
 constexpr int kNoAllocDevices = 64;
 std::mutex g_noalloc_mu;
-double* g_noalloc_addr[kNoAllocDevices];  // device address of the scratch, per device, found on first use
+double* g_noalloc_addr[kNoAllocDevices];            // device address of the scratch, per device, found on first use
+unsigned long long g_noalloc_ctx[kNoAllocDevices];  // id of the CUDA context the address belongs to
 
-// The host name of g_noalloc_scratch is only a stand-in: the kernels need the device address, looked up once per
-// device (with that device current) and cached.
+// id of the current CUDA context (0 if it cannot be read).  A cudaDeviceReset ends the device's primary context and
+// the next runtime call creates a new one, in which the library's module -- and so the array -- may be placed at
+// another address; a changed id makes the lookup below run again instead of handing a stale address to a kernel.
+unsigned long long current_context_id() {
+    typedef int (*get_ctx_t)(void**);
+    typedef int (*get_id_t)(void*, unsigned long long*);
+    static get_ctx_t get_ctx = nullptr;
+    static get_id_t get_id = nullptr;
+    static bool looked_up = false;
+    if (!looked_up) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_ctx = (get_ctx_t)p;
+        p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = (get_id_t)p;
+        looked_up = true;
+    }
+    void* ctx = nullptr;
+    unsigned long long id = 0;
+    if (!get_ctx || !get_id || get_ctx(&ctx) != 0 || !ctx || get_id(ctx, &id) != 0) return 0;
+    return id;
+}
+
+// The host name of g_noalloc_scratch is only a stand-in: the kernels need the device address, looked up with the
+// device current (the runtime makes its context current first) and cached per device and context.
 int noalloc_scratch(double** out) {
     int dev = -1;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
     if (dev < 0 || dev >= kNoAllocDevices) return fail(HG_ERR_ARG, "device index %d out of range", dev);
+    const unsigned long long ctx = current_context_id();  // 0 while no context is current yet
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_addr[dev]) {
+    if (!g_noalloc_addr[dev] || ctx != g_noalloc_ctx[dev]) {
         double* p = nullptr;
-        e = cudaGetSymbolAddress((void**)&p, g_noalloc_scratch);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(moment scratch)");
+        e = cudaGetSymbolAddress((void**)&p, g_noalloc_scratch);  // also creates the context on a first call
+        if (e != cudaSuccess) {
+            g_noalloc_addr[dev] = nullptr;
+            return cuda_fail(e, "cudaGetSymbolAddress(moment scratch)");
+        }
         g_noalloc_addr[dev] = p;
+        g_noalloc_ctx[dev] = current_context_id();
     }
     *out = g_noalloc_addr[dev];
     return HG_OK;
@@ -356,10 +446,10 @@ int noalloc_moments(const void* rho, int dtype, int nx, int ny, int nz, double h
     constexpr int NQ = (LMAX + 1) * (LMAX + 1);
     YlmNorm N;
     fill_ylm_norms(N);
-    k_moments<LMAX><<<kRedBlocks, kRedThreads, 0, st>>>(rho, dtype, nx, ny, nz, h, o[0], o[1], o[2], N, scratch);
+    k_moments<LMAX><<<kMomBlocks, kRedThreads, 0, st>>>(rho, dtype, nx, ny, nz, h, o[0], o[1], o[2], N, scratch);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "multipole moment kernel");
-    k_finish<<<1, kRedThreads, 0, st>>>(scratch, kRedBlocks, NQ, Qdev);
+    k_finish<<<1, kRedThreads, 0, st>>>(scratch, kMomBlocks, NQ, Qdev);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "moment finish kernel");
     return HG_OK;
@@ -370,6 +460,7 @@ int noalloc_moments(const void* rho, int dtype, int nx, int ny, int nz, double h
 
 extern "C" int hg_moments_noalloc(const void* rho, int dtype, int nx, int ny, int nz, double h, const double origin[3],
                                   int lmax, double* Q, int Q_on_device, void* cuda_stream) {
+    HG_RANGE("hg_moments_noalloc");
     using namespace hg;
     if (!rho || !Q || !origin) return fail(HG_ERR_ARG, "null pointer");
     if (dtype != HG_DT_F32 && dtype != HG_DT_F64) return fail(HG_ERR_ARG, "unknown dtype %d", dtype);
@@ -383,7 +474,7 @@ extern "C" int hg_moments_noalloc(const void* rho, int dtype, int nx, int ny, in
     int rc = noalloc_scratch(&scratch);
     if (rc) return rc;
     cudaStream_t st = (cudaStream_t)cuda_stream;
-    double* Qdev = Q_on_device ? Q : scratch + (long long)kRedBlocks * kMaxQ;
+    double* Qdev = Q_on_device ? Q : scratch + 2LL * kMomBlocks * kMaxQ;
     switch (lmax) {
         case 0: rc = noalloc_moments<0>(rho, dtype, nx, ny, nz, h, origin, scratch, Qdev, st); break;
         case 1: rc = noalloc_moments<1>(rho, dtype, nx, ny, nz, h, origin, scratch, Qdev, st); break;

@@ -2,15 +2,16 @@
 
 Such a caller passes its own density and output buffers and gets the same FP64 moments that a grid computes in
 hg_set_density, with the scratch taken from a fixed array inside the library.  Checked through the C ABI against
-hg_get_moments (the existing entry point) at the FP64 tolerance of the other tests, on consecutive calls (the
-shared scratch must not carry anything over from one call to the next) and with the result in device or host
-memory.  This file is collected last so that a failure here does not hide the other tests.
+hg_get_moments (the existing entry point) and against the CPU oracle's moments, at the FP64 tolerance of the
+other tests, on consecutive calls (the shared scratch must not carry anything over from one call to the next) and
+with the result in device or host memory.  This file is collected last so that a failure here does not hide the other tests.
 """
 import ctypes
 
 import numpy as np
 import pytest
 
+import oracle as O
 from paper_1602_05700_gb300 import inputs as I
 
 pytestmark = pytest.mark.gpu
@@ -62,19 +63,29 @@ def close(a, b):
     return np.abs(a - b).max() <= TOL * np.abs(b).max()
 
 
+def oracle_moments(n, rho, lmax):
+    return O.moments(O.unit_cube(n, 1.0, 1.0, 0.5, O.BC_DIRICHLET), rho.double().cpu().numpy(), lmax)
+
+
 def test_matches_grid_moments_on_consecutive_calls():
     n = 48
     rho = torch.from_numpy(I.sphere_density(n) + I.blob_density(n, I.draw_blobs(8, 1))).cuda()
     Q4 = reference(n, rho, 4)
+    assert close(Q4, oracle_moments(n, rho, 4))
     first = noalloc(rho, 4, n, on_device=True)
     second = noalloc(rho, 4, n, on_device=True)
+    O4 = oracle_moments(n, rho, 4)
     assert close(first, Q4) and close(second, Q4)
-    assert close(noalloc(rho, 4, n, on_device=False), Q4)
+    assert close(first, O4) and close(second, O4)
+    assert close(noalloc(rho, 4, n, on_device=False), O4)
     # a different density and order right after: nothing of the previous calls may leak into the result
     rho2 = torch.from_numpy(I.blob_density(n, I.draw_blobs(3, 9))).to(torch.float32).cuda()
     Q8 = reference(n, rho2, 8)
-    assert close(noalloc(rho2, 8, n, on_device=True), Q8)
-    assert close(noalloc(rho2, 8, n, on_device=False), Q8)
+    O8 = oracle_moments(n, rho2, 8)
+    assert close(Q8, O8)
+    for on_device in (True, False):
+        got = noalloc(rho2, 8, n, on_device=on_device)
+        assert close(got, Q8) and close(got, O8)
     assert close(noalloc(rho, 4, n, on_device=True), Q4)
 
 
