@@ -19,6 +19,9 @@ independent problems (weak scaling, no collective on the data path).
 from __future__ import annotations
 
 import argparse
+import collections
+import csv
+import io
 import hashlib
 import json
 import math
@@ -813,6 +816,82 @@ def run_virial(args):
     return res
 
 
+# ---- summaries of Nsight Compute output for the notes under profiles/ ----
+
+NCU_SCALE = {"ns": 1e-6, "nsecond": 1e-6, "us": 1e-3, "usecond": 1e-3, "ms": 1.0, "msecond": 1.0, "s": 1e3, "second": 1e3}
+
+NCU_REPORT_METRICS = [
+    ("gpu__time_duration.sum", "duration"),
+    ("dram__bytes_read.sum", "DRAM read"),
+    ("dram__bytes_write.sum", "DRAM write"),
+    ("gpu__dram_throughput.avg.pct_of_peak_sustained_elapsed", "DRAM throughput % of peak"),
+    ("lts__t_sector_hit_rate.pct", "L2 hit rate %"),
+    ("sm__throughput.avg.pct_of_peak_sustained_elapsed", "SM throughput %"),
+    ("smsp__issue_active.avg.pct_of_peak_sustained_active", "issue active %"),
+    ("sm__pipe_fma_cycles_active.avg.pct_of_peak_sustained_active", "FMA pipe %"),
+    ("sm__pipe_alu_cycles_active.avg.pct_of_peak_sustained_active", "ALU pipe %"),
+    ("sm__pipe_fp64_cycles_active.avg.pct_of_peak_sustained_active", "FP64 pipe %"),
+    ("sm__pipe_tensor_cycles_active.avg.pct_of_peak_sustained_active", "tensor pipe %"),
+    ("sm__warps_active.avg.pct_of_peak_sustained_active", "warps active %"),
+    ("launch__registers_per_thread", "registers/thread"),
+    ("launch__occupancy_limit_registers", "blocks/SM (register limit)"),
+    ("launch__grid_size", "grid"),
+    ("launch__block_size", "block"),
+    ("sm__inst_executed_pipe_lsu.avg.pct_of_peak_sustained_active", "LSU issue %"),
+    ("sm__inst_executed_pipe_xu.avg.pct_of_peak_sustained_active", "XU issue %"),
+    ("sm__inst_executed_pipe_adu.avg.pct_of_peak_sustained_active", "ADU issue %"),
+    ("smsp__average_warps_issue_stalled_long_scoreboard_per_issue_active.ratio", "stall long scoreboard"),
+    ("smsp__average_warps_issue_stalled_short_scoreboard_per_issue_active.ratio", "stall short scoreboard"),
+    ("smsp__average_warps_issue_stalled_wait_per_issue_active.ratio", "stall wait"),
+    ("smsp__average_warps_issue_stalled_lg_throttle_per_issue_active.ratio", "stall LG throttle"),
+    ("smsp__average_warps_issue_stalled_mio_throttle_per_issue_active.ratio", "stall MIO throttle"),
+    ("smsp__average_warps_issue_stalled_not_selected_per_issue_active.ratio", "stall not selected"),
+    ("smsp__average_warps_issue_stalled_barrier_per_issue_active.ratio", "stall barrier"),
+    ("smsp__average_warps_issue_stalled_math_pipe_throttle_per_issue_active.ratio", "stall math pipe"),
+    ("smsp__inst_executed.sum", "warp instructions"),
+]
+
+
+def ncu_short(name: str) -> str:
+    for ns in ("(anonymous namespace)::", "<unnamed>::", "unnamed>::", "hg::"):
+        name = name.replace(ns, "")
+    return name.split("(")[0].replace("void ", "").strip()
+
+
+def ncu_launches(path):
+    """Per-kernel launches, total time and share of an ncu launch list (--metrics gpu__time_duration.sum --csv)."""
+    rows = list(csv.reader(open(path)))
+    h = next(i for i, r in enumerate(rows) if "Kernel Name" in r)
+    hdr = rows[h]
+    ki, vi, ui = hdr.index("Kernel Name"), hdr.index("Metric Value"), hdr.index("Metric Unit")
+    agg = collections.defaultdict(lambda: [0, 0.0])
+    for r in rows[h + 1:]:
+        if len(r) <= vi or not r[vi]:
+            continue
+        agg[ncu_short(r[ki])][0] += 1
+        agg[ncu_short(r[ki])][1] += float(r[vi].replace(",", "")) * NCU_SCALE[r[ui]]
+    tot = sum(a[1] for a in agg.values())
+    print(f"| kernel | launches | total ms | share |\n|---|---|---|---|")
+    for k, (n, t) in sorted(agg.items(), key=lambda x: -x[1][1]):
+        print(f"| `{k}` | {n} | {t:.3f} | {100 * t / tot:.2f}% |")
+    print(f"| total | {sum(a[0] for a in agg.values())} | {tot:.3f} | |")
+
+
+def ncu_report(path):
+    """The headline counters of each launch of an ncu report (read with `ncu -i ... --page raw --csv`)."""
+    out = subprocess.run(["ncu", "-i", path, "--page", "raw", "--csv"], capture_output=True, text=True, check=True)
+    rows = list(csv.reader(io.StringIO(out.stdout)))
+    hdr, units = rows[0], rows[1]
+    for launch in rows[2:]:
+        name = ncu_short(launch[hdr.index("Kernel Name")]) if "Kernel Name" in hdr else "?"
+        print(f"launch: `{name}`\n\n| counter | value |\n|---|---|")
+        for metric, label in NCU_REPORT_METRICS:
+            if metric in hdr:
+                i = hdr.index(metric)
+                print(f"| {label} (`{metric}`) | {launch[i]} {units[i]} |")
+        print()
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -834,7 +913,17 @@ def main():
                     help="headline: the metric's 512^3 line (default); the others print the other workloads")
     ap.add_argument("--substeps", type=int, default=None,
                     help="sub-steps for --config precision/batch/adjoint; hydro steps for --config lag/domain/virial")
+    ap.add_argument("--ncu-launches", metavar="CSV", default=None,
+                    help="summarise an ncu launch list (per kernel: launches, total time, share) and exit")
+    ap.add_argument("--ncu-report", metavar="NCU_REP", default=None,
+                    help="print the headline counters of each launch in an ncu report and exit")
     args = ap.parse_args()
+    if args.ncu_launches or args.ncu_report:
+        if args.ncu_launches:
+            ncu_launches(args.ncu_launches)
+        if args.ncu_report:
+            ncu_report(args.ncu_report)
+        return
     from paper_1602_05700_gb300.multi import env_ranks
 
     rank, world, local_rank = env_ranks()

@@ -191,6 +191,7 @@ void release(hg_batch* b) {
 extern "C" {
 
 int hg_batch_create(hg_grid* const* grids, int n, hg_batch** out) {
+    HG_RANGE("hg_batch_create");
     if (!out) return fail(HG_ERR_ARG, "null output pointer");
     *out = nullptr;
     if (!grids || n < 1) return fail(HG_ERR_ARG, "need at least one grid");
@@ -227,6 +228,7 @@ int hg_batch_create(hg_grid* const* grids, int n, hg_batch** out) {
 }
 
 int hg_batch_step(hg_batch* b, int n_substeps) {
+    HG_RANGE("hg_batch_step");
     if (!b) return fail(HG_ERR_ARG, "null batch");
     if (n_substeps < 0) return fail(HG_ERR_ARG, "n_substeps must be >= 0");
     if (n_substeps == 0) return HG_OK;
@@ -270,6 +272,7 @@ int hg_batch_step(hg_batch* b, int n_substeps) {
 }
 
 int hg_batch_info(const hg_batch* b, int* z_planes_per_block, long long* blocks_per_substep) {
+    HG_RANGE("hg_batch_info");
     if (!b) return fail(HG_ERR_ARG, "null batch");
     if (z_planes_per_block) *z_planes_per_block = b->zb;
     if (blocks_per_substep) *blocks_per_substep = b->total_blocks;
@@ -277,6 +280,7 @@ int hg_batch_info(const hg_batch* b, int* z_planes_per_block, long long* blocks_
 }
 
 void hg_batch_free(hg_batch* b) {
+    HG_RANGE("hg_batch_free");
     if (!b) return;
     cudaSetDevice(b->device);
     cudaStreamSynchronize(b->stream);

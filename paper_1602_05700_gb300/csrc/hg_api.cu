@@ -295,6 +295,7 @@ static int set_density_device(hg_grid* g, const void* src, int dtype) {
 }
 
 int hg_set_density(hg_grid* g, const void* rho, int dtype, int on_device) {
+    HG_RANGE("hg_set_density");
     int rc = check_grid(g);
     if (rc) return rc;
     if (!rho) return fail(HG_ERR_ARG, "null density");
@@ -312,6 +313,7 @@ int hg_set_density(hg_grid* g, const void* rho, int dtype, int on_device) {
 }
 
 int hg_set_phi(hg_grid* g, const void* phi, const void* phi_prev, int dtype, int on_device) {
+    HG_RANGE("hg_set_phi");
     int rc = check_grid(g);
     if (rc) return rc;
     if (!phi) return fail(HG_ERR_ARG, "null phi");
@@ -337,6 +339,7 @@ int hg_set_phi(hg_grid* g, const void* phi, const void* phi_prev, int dtype, int
 }
 
 int hg_set_temporal_depth(hg_grid* g, int k) {
+    HG_RANGE("hg_set_temporal_depth");
     int rc = check_grid(g);
     if (rc) return rc;
     if (k < 1 || k > HG_MAX_TEMPORAL_DEPTH)
@@ -354,6 +357,7 @@ int hg_set_temporal_depth(hg_grid* g, int k) {
 }
 
 int hg_set_block_depth(hg_grid* g, int planes) {
+    HG_RANGE("hg_set_block_depth");
     int rc = check_grid(g);
     if (rc) return rc;
     if (planes < 0) return fail(HG_ERR_ARG, "planes must be >= 0");
@@ -362,6 +366,7 @@ int hg_set_block_depth(hg_grid* g, int planes) {
 }
 
 int hg_step(hg_grid* g, int n_substeps) {
+    HG_RANGE("hg_step");
     int rc = check_grid(g);
     if (rc) return rc;
     if (n_substeps < 0) return fail(HG_ERR_ARG, "n_substeps must be >= 0");
@@ -383,6 +388,7 @@ int hg_step(hg_grid* g, int n_substeps) {
 }
 
 int hg_accel(hg_grid* g, void* ax, void* ay, void* az, int dtype) {
+    HG_RANGE("hg_accel");
     int rc = check_grid(g);
     if (rc) return rc;
     if (!ax || !ay || !az) return fail(HG_ERR_ARG, "null acceleration buffer");
@@ -391,6 +397,7 @@ int hg_accel(hg_grid* g, void* ax, void* ay, void* az, int dtype) {
 }
 
 int hg_get_phi(hg_grid* g, void* out, int dtype, int on_device) {
+    HG_RANGE("hg_get_phi");
     int rc = check_grid(g);
     if (rc) return rc;
     if (!out) return fail(HG_ERR_ARG, "null output");
@@ -405,6 +412,7 @@ int hg_get_phi(hg_grid* g, void* out, int dtype, int on_device) {
 }
 
 int hg_get_phi_ghosted(hg_grid* g, double* out) {
+    HG_RANGE("hg_get_phi_ghosted");
     int rc = check_grid(g);
     if (rc) return rc;
     if (!out) return fail(HG_ERR_ARG, "null output");
@@ -417,6 +425,7 @@ int hg_get_phi_ghosted(hg_grid* g, double* out) {
 }
 
 int hg_get_stats(hg_grid* g, hg_stats* s) {
+    HG_RANGE("hg_get_stats");
     int rc = check_grid(g);
     if (rc) return rc;
     if (!s) return fail(HG_ERR_ARG, "null stats");
@@ -426,6 +435,7 @@ int hg_get_stats(hg_grid* g, hg_stats* s) {
 }
 
 int hg_get_moments(hg_grid* g, double* Q) {
+    HG_RANGE("hg_get_moments");
     int rc = check_grid(g);
     if (rc) return rc;
     if (!Q) return fail(HG_ERR_ARG, "null output");
@@ -437,6 +447,7 @@ int hg_get_moments(hg_grid* g, double* Q) {
 }
 
 int hg_compare(hg_grid* g, const double* phi_P, int on_device, double out[3]) {
+    HG_RANGE("hg_compare");
     int rc = check_grid(g);
     if (rc) return rc;
     if (!phi_P || !out) return fail(HG_ERR_ARG, "null argument");
@@ -451,13 +462,19 @@ int hg_compare(hg_grid* g, const double* phi_P, int on_device, double out[3]) {
 }
 
 // ---- checkpoint / resume ----
+// The stored source s = (c_h dt)^2 4 pi G (rho - rho_bar), the Dirichlet ghosts (functions of h, the origin and G)
+// and the Robin coefficients (functions of nu = c_h dt / h and the geometry) are only valid for the grid that wrote
+// them, so the header records every parameter they depend on and a load accepts only a bit-identical match.
 struct StateHeader {
     char magic[8];
     int nx, ny, nz, prec, bc, lmax, cur, have_Q;
     long long step;
     double mass, rho_bar;
+    double h, origin[3], c, G, dt;
     double Q[kMaxQ];
 };
+
+static bool same_bits(double a, double b) { return memcmp(&a, &b, sizeof a) == 0; }
 
 static int n_buffers(const hg_grid* g) { return g->prec == HG_PREC_F64 ? 3 : 6; }
 static void** buffer(hg_grid* g, int b) {
@@ -469,6 +486,7 @@ static size_t buffer_bytes(const hg_grid* g, int b) {
 }
 
 size_t hg_state_bytes(const hg_grid* g) {
+    HG_RANGE("hg_state_bytes");
     if (!g) return 0;
     size_t n = sizeof(StateHeader);
     for (int b = 0; b < n_buffers(g); ++b) n += buffer_bytes(g, b);
@@ -476,13 +494,14 @@ size_t hg_state_bytes(const hg_grid* g) {
 }
 
 int hg_save_state(hg_grid* g, void* buf, int on_device) {
+    HG_RANGE("hg_save_state");
     int rc = check_grid(g);
     if (rc) return rc;
     if (!buf) return fail(HG_ERR_ARG, "null buffer");
     const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     StateHeader H;
     memset(&H, 0, sizeof H);
-    memcpy(H.magic, "HGSTATE1", 8);
+    memcpy(H.magic, "HGSTATE2", 8);
     H.nx = g->nx;
     H.ny = g->ny;
     H.nz = g->nz;
@@ -492,6 +511,11 @@ int hg_save_state(hg_grid* g, void* buf, int on_device) {
     H.cur = g->cur;
     H.have_Q = g->have_Q;
     H.step = g->step;
+    H.h = g->h;
+    for (int a = 0; a < 3; ++a) H.origin[a] = g->origin[a];
+    H.c = g->c;
+    H.G = g->G;
+    H.dt = g->dt;
     if ((rc = sync_mass(g))) return rc;
     H.mass = g->mass;
     H.rho_bar = g->rho_bar;
@@ -510,6 +534,7 @@ int hg_save_state(hg_grid* g, void* buf, int on_device) {
 }
 
 int hg_load_state(hg_grid* g, const void* buf, int on_device) {
+    HG_RANGE("hg_load_state");
     int rc = check_grid(g);
     if (rc) return rc;
     if (!buf) return fail(HG_ERR_ARG, "null buffer");
@@ -521,9 +546,13 @@ int hg_load_state(hg_grid* g, const void* buf, int on_device) {
     } else {
         memcpy(&H, buf, sizeof H);
     }
-    if (memcmp(H.magic, "HGSTATE1", 8) != 0 || H.nx != g->nx || H.ny != g->ny || H.nz != g->nz || H.prec != g->prec ||
+    if (memcmp(H.magic, "HGSTATE2", 8) != 0 || H.nx != g->nx || H.ny != g->ny || H.nz != g->nz || H.prec != g->prec ||
         H.bc != g->bc || H.lmax != g->lmax)
         return fail(HG_ERR_ARG, "state buffer does not match this grid");
+    if (!same_bits(H.h, g->h) || !same_bits(H.origin[0], g->origin[0]) || !same_bits(H.origin[1], g->origin[1]) ||
+        !same_bits(H.origin[2], g->origin[2]) || !same_bits(H.c, g->c) || !same_bits(H.G, g->G) ||
+        !same_bits(H.dt, g->dt))
+        return fail(HG_ERR_ARG, "state buffer was written by a grid with another h, origin, c_h, G or dt");
     const char* p = (const char*)buf + sizeof H;
     for (int b = 0; b < n_buffers(g); ++b) {
         HG_CUDA(cudaMemcpyAsync(*buffer(g, b), p, buffer_bytes(g, b), kind, g->stream));
@@ -541,6 +570,7 @@ int hg_load_state(hg_grid* g, const void* buf, int on_device) {
 }
 
 int hg_profile(hg_grid* g, int enable) {
+    HG_RANGE("hg_profile");
     int rc = check_grid(g);
     if (rc) return rc;
     if (enable && !g->prof_ev) {
@@ -553,6 +583,7 @@ int hg_profile(hg_grid* g, int enable) {
 }
 
 int hg_profile_read(hg_grid* g, double* substep_kernel_ms, long long* substep_launches, long long* kernel_launches) {
+    HG_RANGE("hg_profile_read");
     int rc = check_grid(g);
     if (rc) return rc;
     if ((rc = prof_fold(g))) return rc;
@@ -566,6 +597,7 @@ int hg_profile_read(hg_grid* g, double* substep_kernel_ms, long long* substep_la
 
 // ---- adjoint ----
 int hg_adjoint_reset(hg_grid* g) {
+    HG_RANGE("hg_adjoint_reset");
     int rc = check_grid(g);
     if (rc) return rc;
     if (!g->adj) {
@@ -593,6 +625,7 @@ int hg_adjoint_reset(hg_grid* g) {
 }
 
 int hg_adjoint_inject(hg_grid* g, const void* dL_dphi, int dtype, int on_device) {
+    HG_RANGE("hg_adjoint_inject");
     int rc = check_grid(g);
     if (rc) return rc;
     if (!g->adj) return fail(HG_ERR_STATE, "call hg_adjoint_reset first");
@@ -614,6 +647,7 @@ int hg_adjoint_inject(hg_grid* g, const void* dL_dphi, int dtype, int on_device)
 }
 
 int hg_adjoint_step(hg_grid* g, int n_substeps) {
+    HG_RANGE("hg_adjoint_step");
     int rc = check_grid(g);
     if (rc) return rc;
     if (!g->adj) return fail(HG_ERR_STATE, "call hg_adjoint_reset first");
@@ -629,6 +663,7 @@ int hg_adjoint_step(hg_grid* g, int n_substeps) {
 }
 
 int hg_adjoint_grad(hg_grid* g, void* dL_drho, int dtype, int on_device) {
+    HG_RANGE("hg_adjoint_grad");
     int rc = check_grid(g);
     if (rc) return rc;
     if (!g->adj) return fail(HG_ERR_STATE, "call hg_adjoint_reset first");
@@ -682,6 +717,7 @@ static int io_ready(hg_grid* g, size_t rho_bytes, size_t acc_bytes) {
 }
 
 int hg_adjoint(hg_grid* g, const void* dL_dphiT, int T, void* dL_drho, int dtype, int on_device) {
+    HG_RANGE("hg_adjoint");
     int rc = check_grid(g);
     if (rc) return rc;
     if (!dL_dphiT || !dL_drho) return fail(HG_ERR_ARG, "null adjoint buffer");
@@ -694,6 +730,7 @@ int hg_adjoint(hg_grid* g, const void* dL_dphiT, int T, void* dL_drho, int dtype
 
 int hg_io_step(hg_grid* g, const void* rho_host, int rho_dtype, int n_substeps, void* ax_host, void* ay_host,
                void* az_host, int acc_dtype) {
+    HG_RANGE("hg_io_step");
     int rc = check_grid(g);
     if (rc) return rc;
     if (n_substeps < 0) return fail(HG_ERR_ARG, "n_substeps must be >= 0");
@@ -741,6 +778,7 @@ int hg_io_step(hg_grid* g, const void* rho_host, int rho_dtype, int n_substeps, 
 }
 
 int hg_io_wait(hg_grid* g, int keep) {
+    HG_RANGE("hg_io_wait");
     int rc = check_grid(g);
     if (rc) return rc;
     if (keep < 0) return fail(HG_ERR_ARG, "keep must be >= 0");
@@ -754,6 +792,7 @@ int hg_io_wait(hg_grid* g, int keep) {
 }
 
 int hg_check_bounded_wait(hg_grid* g) {
+    HG_RANGE("hg_check_bounded_wait");
     int rc = check_grid(g);
     if (rc) return rc;
     if ((rc = device_error(g))) return rc;  // an earlier error is reported as such, not taken for the self-test's
@@ -764,6 +803,7 @@ int hg_check_bounded_wait(hg_grid* g) {
 }
 
 int hg_sync(hg_grid* g) {
+    HG_RANGE("hg_sync");
     int rc = check_grid(g);
     if (rc) return rc;
     HG_CUDA(cudaStreamSynchronize(g->stream));
@@ -778,6 +818,7 @@ int hg_sync(hg_grid* g) {
 }
 
 void hg_free(hg_grid* g) {
+    HG_RANGE("hg_free");
     if (!g) return;
     cudaSetDevice(g->device);
     cudaStreamSynchronize(g->stream);

@@ -1,6 +1,8 @@
 // Internal definitions shared by the translation units of the CUDA library (not part of the C ABI).
 #pragma once
 
+#include <nvtx3/nvToolsExt.h>
+
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -10,6 +12,17 @@
 #include "hg.h"
 
 namespace hg {
+
+// An NVTX range around every ABI call, so that a profiler's timeline shows which call enqueued which kernels (a
+// push and a pop of a named range; without an attached tool both return at once).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
+#define HG_RANGE(name) ::hg::NvtxRange hg_nvtx_range_(name)
+
 
 // ---- device memory layout ------------------------------------------------------------------------------------
 // Every per-cell field of a grid lives in one "padded" array of pitch * (ny+2) * (nz+2) elements: z-planes of

@@ -238,6 +238,7 @@ extern "C" {
 
 int hg_hydro_init(hg_hydro** out, int nx, int ny, int nz, double h, double gamma, double rho_floor, double p_floor,
                   int dtype, void* cuda_stream) {
+    HG_RANGE("hg_hydro_init");
     if (!out) return fail(HG_ERR_ARG, "null output handle");
     *out = nullptr;
     if (nx < 1 || ny < 1 || nz < 1) return fail(HG_ERR_ARG, "grid sizes must be >= 1 (got %d %d %d)", nx, ny, nz);
@@ -276,6 +277,7 @@ int hg_hydro_init(hg_hydro** out, int nx, int ny, int nz, double h, double gamma
 }
 
 int hg_hydro_set_primitive(hg_hydro* H, const void* W, int dtype, int on_device) {
+    HG_RANGE("hg_hydro_set_primitive");
     int rc = check_hydro(H);
     if (rc) return rc;
     if (!W) return fail(HG_ERR_ARG, "null primitive fields");
@@ -293,6 +295,7 @@ int hg_hydro_set_primitive(hg_hydro* H, const void* W, int dtype, int on_device)
 }
 
 int hg_hydro_set_state(hg_hydro* H, const void* U, int dtype, int on_device) {
+    HG_RANGE("hg_hydro_set_state");
     int rc = check_hydro(H);
     if (rc) return rc;
     if (!U) return fail(HG_ERR_ARG, "null state");
@@ -304,6 +307,7 @@ int hg_hydro_set_state(hg_hydro* H, const void* U, int dtype, int on_device) {
 }
 
 int hg_hydro_get_state(hg_hydro* H, void* U, int dtype, int on_device) {
+    HG_RANGE("hg_hydro_get_state");
     int rc = check_hydro(H);
     if (rc) return rc;
     if (!U) return fail(HG_ERR_ARG, "null output");
@@ -315,6 +319,7 @@ int hg_hydro_get_state(hg_hydro* H, void* U, int dtype, int on_device) {
 }
 
 int hg_hydro_max_speed(hg_hydro* H, double* s) {
+    HG_RANGE("hg_hydro_max_speed");
     int rc = check_hydro(H);
     if (rc) return rc;
     if (!s) return fail(HG_ERR_ARG, "null output");
@@ -333,6 +338,7 @@ int hg_hydro_max_speed(hg_hydro* H, double* s) {
 }
 
 int hg_hydro_step(hg_hydro* H, hg_grid* g, double dt, int n_substeps) {
+    HG_RANGE("hg_hydro_step");
     int rc = check_hydro(H);
     if (rc) return rc;
     if (!(dt > 0.0)) return fail(HG_ERR_ARG, "dt must be > 0");
@@ -351,6 +357,7 @@ int hg_hydro_step(hg_hydro* H, hg_grid* g, double dt, int n_substeps) {
 }
 
 int hg_hydro_virial(hg_hydro* H, hg_grid* g, double out[6]) {
+    HG_RANGE("hg_hydro_virial");
     int rc = check_hydro(H);
     if (rc) return rc;
     if (!g || !out) return fail(HG_ERR_ARG, "null grid or output");
@@ -380,12 +387,14 @@ int hg_hydro_virial(hg_hydro* H, hg_grid* g, double out[6]) {
 }
 
 int hg_hydro_launches(hg_hydro* H, long long* n) {
+    HG_RANGE("hg_hydro_launches");
     if (!H || !n) return fail(HG_ERR_ARG, "null argument");
     *n = H->launches;
     return HG_OK;
 }
 
 int hg_hydro_profile(hg_hydro* H, int enable) {
+    HG_RANGE("hg_hydro_profile");
     int rc = check_hydro(H);
     if (rc) return rc;
     if (enable && !H->prof_ev) {
@@ -398,6 +407,7 @@ int hg_hydro_profile(hg_hydro* H, int enable) {
 }
 
 int hg_hydro_profile_read(hg_hydro* H, double* stage_ms, long long* stage_launches) {
+    HG_RANGE("hg_hydro_profile_read");
     int rc = check_hydro(H);
     if (rc) return rc;
     if ((rc = hydro_prof_fold(H))) return rc;
@@ -409,6 +419,7 @@ int hg_hydro_profile_read(hg_hydro* H, double* stage_ms, long long* stage_launch
 }
 
 void hg_hydro_free(hg_hydro* H) {
+    HG_RANGE("hg_hydro_free");
     if (!H) return;
     cudaSetDevice(H->device);
     cudaStreamSynchronize(H->stream);

@@ -215,6 +215,36 @@ def test_checkpoint_resume_bit_exact():
     assert np.array_equal(a, b)
 
 
+def test_load_state_rejects_other_grid_parameters():
+    """A checkpoint carries the scaled source, the Dirichlet data and the Robin coefficients of the grid that wrote
+    it; a grid of the same shape but another dt, c_h, G, h or origin must refuse it and keep its own state."""
+    n = 16
+    h = 1.0 / n
+    o = (-0.5, -0.5, -0.5)
+    dt = 0.5 * h / np.sqrt(3.0)
+    g = hg.Grid(n, n, n, h, o, 1.0, 1.0, dt, "f64", "robin")
+    g.set_density(I.sphere_density(n))
+    g.step(5)
+    blob = g.save_state()
+    others = [hg.Grid(n, n, n, h, o, 1.0, 1.0, dt * 0.5, "f64", "robin"),
+              hg.Grid(n, n, n, h, o, 0.5, 1.0, dt, "f64", "robin"),
+              hg.Grid(n, n, n, h, o, 1.0, 2.0, dt, "f64", "robin"),
+              hg.Grid(n, n, n, h * 0.5, (-0.25, -0.25, -0.25), 1.0, 1.0, dt * 0.5, "f64", "robin"),
+              hg.Grid(n, n, n, h, (-0.5, -0.5, -0.5 + h), 1.0, 1.0, dt, "f64", "robin")]
+    for g2 in others:
+        g2.set_density(I.sphere_density(n))
+        g2.step(2)
+        before = g2.phi(torch.float64, "cpu")
+        with pytest.raises(hg.HGError):
+            g2.load_state(blob)
+        assert np.array_equal(g2.phi(torch.float64, "cpu"), before)
+        assert g2.stats()["step"] == 2
+        g2.free()
+    g3 = hg.Grid(n, n, n, h, o, 1.0, 1.0, dt, "f64", "robin")
+    g3.load_state(blob)
+    assert np.array_equal(g3.phi(torch.float64, "cpu"), g.phi(torch.float64, "cpu"))
+
+
 def test_errors_reported_not_raised_on_device():
     n = 16
     g = hg.Grid.unit_cube(n, 1.0, 1.0, 0.5, "f32k", "robin")
