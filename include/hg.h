@@ -280,6 +280,15 @@ void hg_batch_free(hg_batch* b);
 int hg_moments_noalloc(const void* rho, int dtype, int nx, int ny, int nz, double h, const double origin[3], int lmax,
                        double* Q, int Q_on_device, void* cuda_stream);
 
+/*
+ * Measured arithmetic rate of the current GPU (a measurement aid for the rooflines of pipe-bound kernels; the paper
+ * has no counterpart): kind 0 = FP64 fused multiply-add, 1 = FP32 fused multiply-add, 2 = the packed FP32 pair
+ * (two multiply-adds in one instruction).  Independent dependency chains on 8 blocks of 256 threads per SM, best of
+ * five event-timed launches after a warm-up.  instr_per_s: thread-level instructions per second; ops_per_s
+ * (may be NULL): multiply-adds per second.  Synchronous (its own stream).  Errors: HG_ERR_ARG, HG_ERR_CUDA.
+ */
+int hg_probe_rate(int kind, double* instr_per_s, double* ops_per_s);
+
 /* Message of the last failing call on this host thread ("" if none). */
 const char* hg_last_error(void);
 

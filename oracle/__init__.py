@@ -35,18 +35,35 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRCS = [os.path.join(_HERE, "hg_oracle.c"), os.path.join(_HERE, "hydro_oracle.c")]
 _LIB_DIR = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_LIB_DIR, "libhgoracle.so")
+_LIB_OMP = os.path.join(_LIB_DIR, "libhgoracle_omp.so")
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle's C files with gcc (-O2, no FMA contraction, no fast-math) into oracle/_build/."""
-    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= max(os.path.getmtime(f) for f in _SRCS):
-        return _LIB
+def build(force: bool = False, openmp: bool = False) -> str:
+    """Compile the oracle's C files with gcc (-O2, no FMA contraction, no fast-math) into oracle/_build/.  With
+    openmp=True, a second library of the same files built with -fopenmp (the sweep split over the host cores), used
+    only to time the oracle on all cores; the checked oracle is the single-threaded build."""
+    lib = _LIB_OMP if openmp else _LIB
+    if not force and os.path.exists(lib) and os.path.getmtime(lib) >= max(os.path.getmtime(f) for f in _SRCS):
+        return lib
     os.makedirs(_LIB_DIR, exist_ok=True)
-    tmp = _LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     subprocess.check_call(["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
-                           "-o", tmp, *_SRCS, "-lm"])
-    os.replace(tmp, _LIB)
-    return _LIB
+                           *(["-fopenmp"] if openmp else []), "-o", tmp, *_SRCS, "-lm"])
+    os.replace(tmp, lib)
+    return lib
+
+
+def run_all_cores(g: "Grid", phi: np.ndarray, phi_prev: np.ndarray, rho: np.ndarray, nsteps: int,
+                  threads: int) -> None:
+    """og_run from the OpenMP build (timing only): the same sub-steps as run(), split over `threads` host cores."""
+    os.environ["OMP_NUM_THREADS"] = str(threads)
+    lib = ctypes.CDLL(build(openmp=True))
+    ctypes.CDLL("libgomp.so.1").omp_set_num_threads(int(threads))
+    P = ctypes.POINTER(ctypes.c_double)
+    lib.og_run.argtypes = [ctypes.POINTER(_OgGrid), P, P, P, ctypes.c_int, P]
+    work = np.zeros(g.ghosted_shape)
+    lib.og_run(ctypes.byref(g._s()), _p(phi), _p(phi_prev), _p(np.ascontiguousarray(rho, dtype=np.float64)),
+               int(nsteps), _p(work))
 
 
 class _OgGrid(ctypes.Structure):

@@ -39,6 +39,15 @@ def build(force: bool = False) -> str:
     return _b(force=force)
 
 
+def probe_rate(kind: str) -> dict:
+    """Measured arithmetic rate of the current GPU (hg_probe_rate): kind "f64", "f32" or "f32x2" (the packed pair).
+    Returns thread instructions/s and multiply-adds/s."""
+    code = {"f64": 0, "f32": 1, "f32x2": 2}[kind]
+    ins, ops = ctypes.c_double(), ctypes.c_double()
+    _lib.check(_lib.lib().hg_probe_rate(code, ctypes.byref(ins), ctypes.byref(ops)))
+    return {"instr_per_s": ins.value, "fma_per_s": ops.value}
+
+
 def _torch():
     import torch
     return torch

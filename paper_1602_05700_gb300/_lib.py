@@ -82,6 +82,7 @@ SIGNATURES = {
     "hg_batch_info": (_I, [_V, _P(_I), _P(ctypes.c_longlong)]),
     "hg_batch_free": (None, [_V]),
     "hg_moments_noalloc": (_I, [_V, _I, _I, _I, _I, _D, _P(_D), _I, _V, _I, _V]),
+    "hg_probe_rate": (_I, [_I, _P(_D), _P(_D)]),
     "hg_last_error": (ctypes.c_char_p, []),
     # include/hg_hydro.h
     "hg_hydro_init": (_I, [_P(_V), _I, _I, _I, _D, _D, _D, _D, _I, _V]),

@@ -447,3 +447,17 @@ def test_exact_sum_is_the_correctly_rounded_sum():
     rho = rng.random((8, 8, 8))
     assert O.mass(g, rho) == math.fsum(rho.ravel()) * g.h * g.h * g.h
     assert O.mean(g, rho) == math.fsum(rho.ravel()) / rho.size
+
+
+@pytest.mark.parametrize("bc", [O.BC_ROBIN, O.BC_PERIODIC, O.BC_DIRICHLET])
+def test_all_core_timing_build_computes_the_same_bits(bc):
+    """The benchmark times the oracle on all host cores with an OpenMP build of the same C file; it must compute
+    exactly what the checked single-threaded oracle computes."""
+    n = 20
+    g = O.unit_cube(n, 1.0, 1.0, 0.5, bc, ny=17, nz=23)
+    rho = I.blob_density(n, I.draw_blobs(3, 4), 17, 23) + 0.1
+    p, q = O.initial_state(g, rho, lmax=2)
+    p2, q2 = p.copy(), q.copy()
+    O.run(g, p, q, rho, 30)
+    O.run_all_cores(g, p2, q2, rho, 30, threads=4)
+    assert np.array_equal(p, p2) and np.array_equal(q, q2)
