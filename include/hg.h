@@ -281,6 +281,36 @@ int hg_moments_noalloc(const void* rho, int dtype, int nx, int ny, int nz, doubl
                        double* Q, int Q_on_device, void* cuda_stream);
 
 /*
+ * Slab decomposition of one grid along z.  The paper notes that the method needs only communication between
+ * neighbouring cells, which suits distributed memory (Sec. 4, timing discussion; Sec. 5).  A grid of nz planes is
+ * split into slabs of consecutive planes, each an hg_grid of its own (origin shifted by k0 h along z, same h, c_h,
+ * G, dt, precision, boundary condition), one per device or process.  Before every sub-step each slab's interface
+ * ghost planes must hold the neighbouring slabs' boundary planes of phi^n:
+ *   hg_set_z_interface(g, lo, hi)      lo / hi = 1: the -z / +z face is an interface (0: an outer face of the whole
+ *                                      grid, updated by the boundary condition as usual).  Robin and Dirichlet
+ *                                      boundaries only (HG_ERR_STATE for periodic), temporal depth 1 only (the
+ *                                      exchange is per sub-step), no batches, no adjoint.
+ *   hg_plane_bytes(g)                  size of one packed plane: nx*ny doubles (F64), or nx*ny floats followed by nx*ny
+ *                                      16-bit compensation codes (F32K).
+ *   hg_get_plane(g, which, buf, dev)   copies the first (which = 0, k = 0) or last (which = 1, k = nz-1) interior
+ *                                      plane of phi^n into buf (device memory if dev, else host; host copies return
+ *                                      after the copy, device copies are ordered on the grid's stream).
+ *   hg_put_ghost_plane(g, side, buf, dev)  copies a packed plane into the -z (side 0) or +z (side 1) ghost plane of
+ *                                      phi^n; HG_ERR_STATE unless that face is an interface.
+ *   hg_set_boundary_moments(g, Q)      Dirichlet modes: evaluates the face ghosts (both time levels) from given
+ *                                      moments Q ((lmax+1)^2 doubles, host memory) -- the sum over all slabs of their
+ *                                      own moments (hg_get_moments after hg_set_density), so that every slab's outer
+ *                                      faces see the expansion of the whole density.
+ * With these, k sub-steps of the slabs (exchange, then hg_step(g, 1) on every slab, k times) reproduce k sub-steps of
+ * the whole grid bit for bit (Robin; Dirichlet up to the rounding of the summed moments).
+ */
+int hg_set_z_interface(hg_grid* g, int lo, int hi);
+size_t hg_plane_bytes(const hg_grid* g);
+int hg_get_plane(hg_grid* g, int which, void* buf, int on_device);
+int hg_put_ghost_plane(hg_grid* g, int side, const void* buf, int on_device);
+int hg_set_boundary_moments(hg_grid* g, const double* Q);
+
+/*
  * Measured arithmetic rate of the current GPU (a measurement aid for the rooflines of pipe-bound kernels; the paper
  * has no counterpart): kind 0 = FP64 fused multiply-add, 1 = FP32 fused multiply-add, 2 = the packed FP32 pair
  * (two multiply-adds in one instruction).  Independent dependency chains on 8 blocks of 256 threads per SM, best of

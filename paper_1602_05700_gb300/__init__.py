@@ -230,6 +230,11 @@ class Grid:
             _lib.check(rc)
         return {k: getattr(s, k) for k, _ in _lib.hg_stats._fields_} | {"rc": rc}
 
+    def set_boundary_moments(self, Q) -> None:
+        """Dirichlet modes: face ghosts from given moments (e.g. the sum of several slabs' own moments)."""
+        Q = np.ascontiguousarray(Q, dtype=np.float64)
+        _lib.check(_lib.lib().hg_set_boundary_moments(self.handle, Q.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+
     def moments(self) -> np.ndarray:
         nq = (self.lmax + 1) ** 2 if self.bc == HG_BC_DIRICHLET_MULTIPOLE else 1
         out = np.zeros(nq)

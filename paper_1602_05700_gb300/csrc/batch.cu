@@ -198,6 +198,7 @@ int hg_batch_create(hg_grid* const* grids, int n, hg_batch** out) {
     for (int i = 0; i < n; ++i) {
         if (!grids[i]) return fail(HG_ERR_ARG, "grid %d is null", i);
         if (grids[i]->device != grids[0]->device) return fail(HG_ERR_ARG, "all grids of a batch must share one device");
+        if (grids[i]->ziface) return fail(HG_ERR_ARG, "grid %d is a slab (z interfaces): batches hold whole grids", i);
         if (grids[i]->stream != grids[0]->stream) return fail(HG_ERR_ARG, "all grids of a batch must share one stream");
         for (int j = 0; j < i; ++j)
             if (grids[j] == grids[i]) return fail(HG_ERR_ARG, "grid %d appears twice", i);

@@ -344,6 +344,8 @@ int hg_set_temporal_depth(hg_grid* g, int k) {
     if (rc) return rc;
     if (k < 1 || k > HG_MAX_TEMPORAL_DEPTH)
         return fail(HG_ERR_ARG, "temporal depth must be in 1..%d", HG_MAX_TEMPORAL_DEPTH);
+    if (k > 1 && g->ziface)
+        return fail(HG_ERR_STATE, "a slab exchanges its interface planes before every sub-step: temporal depth 1 only");
     if (k > 1 && g->prec != HG_PREC_F32K)
         return fail(HG_ERR_ARG, "temporal blocking is built for HG_PREC_F32K only (FP64 sub-steps are bound by the "
                                 "FP64 pipe, not by HBM traffic, so fusing them saves nothing)");
@@ -444,6 +446,85 @@ int hg_get_moments(hg_grid* g, double* Q) {
     int nq = (g->lmax + 1) * (g->lmax + 1);
     for (int q = 0; q < nq; ++q) Q[q] = g->Q[q];
     return HG_OK;
+}
+
+// ---- slab decomposition along z (one grid split over several grids, one per device or process) ----
+int hg_set_z_interface(hg_grid* g, int lo, int hi) {
+    HG_RANGE("hg_set_z_interface");
+    int rc = check_grid(g);
+    if (rc) return rc;
+    if ((lo || hi) && g->bc == HG_BC_PERIODIC)
+        return fail(HG_ERR_STATE, "slab interfaces are built for the Robin and Dirichlet boundaries (a periodic "
+                                  "source needs the mean density of the whole grid)");
+    if ((lo || hi) && g->tdepth > 1)
+        return fail(HG_ERR_STATE, "a slab exchanges its interface planes before every sub-step: temporal depth 1 only");
+    g->ziface = (lo ? 1 : 0) | (hi ? 2 : 0);
+    return HG_OK;
+}
+
+size_t hg_plane_bytes(const hg_grid* g) {
+    HG_RANGE("hg_plane_bytes");
+    if (!g) return 0;
+    const size_t n = (size_t)g->nx * g->ny;
+    return g->prec == HG_PREC_F64 ? n * sizeof(double) : n * (sizeof(float) + sizeof(lo_code));
+}
+
+// one z-plane k of phi^n between the padded state and a packed buffer (F64: nx*ny doubles; F32K: nx*ny floats, then
+// nx*ny compensation codes), with 2-D copies on the grid's stream
+static int plane_copy(hg_grid* g, int k, void* buf, int on_device, bool to_state) {
+    const int c = g->cur;
+    const size_t n = (size_t)g->nx * g->ny;
+    const Layout& L = g->L;
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice
+                                          : (to_state ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToHost);
+    char* b = (char*)buf;
+    const size_t es = (size_t)g->esize;
+    char* hi = (char*)g->phi[c] + (size_t)L.at(0, 0, k) * es;
+    if (to_state)
+        HG_CUDA(cudaMemcpy2DAsync(hi, L.pitch * es, b, g->nx * es, g->nx * es, g->ny, kind, g->stream));
+    else
+        HG_CUDA(cudaMemcpy2DAsync(b, g->nx * es, hi, L.pitch * es, g->nx * es, g->ny, kind, g->stream));
+    if (g->prec == HG_PREC_F32K) {
+        const size_t ls = sizeof(lo_code);
+        char* lo = (char*)g->lo[c] + (size_t)L.at(0, 0, k) * ls;
+        char* bl = b + n * es;
+        if (to_state)
+            HG_CUDA(cudaMemcpy2DAsync(lo, L.pitch * ls, bl, g->nx * ls, g->nx * ls, g->ny, kind, g->stream));
+        else
+            HG_CUDA(cudaMemcpy2DAsync(bl, g->nx * ls, lo, L.pitch * ls, g->nx * ls, g->ny, kind, g->stream));
+    }
+    if (!on_device) HG_CUDA(cudaStreamSynchronize(g->stream));
+    return HG_OK;
+}
+
+int hg_get_plane(hg_grid* g, int which, void* buf, int on_device) {
+    HG_RANGE("hg_get_plane");
+    int rc = check_grid(g);
+    if (rc) return rc;
+    if (!buf || (which != 0 && which != 1)) return fail(HG_ERR_ARG, "null buffer, or which not 0 or 1");
+    return plane_copy(g, which ? g->nz - 1 : 0, buf, on_device, false);
+}
+
+int hg_put_ghost_plane(hg_grid* g, int side, const void* buf, int on_device) {
+    HG_RANGE("hg_put_ghost_plane");
+    int rc = check_grid(g);
+    if (rc) return rc;
+    if (!buf || (side != 0 && side != 1)) return fail(HG_ERR_ARG, "null buffer, or side not 0 or 1");
+    if (!(g->ziface & (1 << side))) return fail(HG_ERR_STATE, "that z face is not a slab interface");
+    return plane_copy(g, side ? g->nz : -1, const_cast<void*>(buf), on_device, true);
+}
+
+int hg_set_boundary_moments(hg_grid* g, const double* Q) {
+    HG_RANGE("hg_set_boundary_moments");
+    int rc = check_grid(g);
+    if (rc) return rc;
+    if (!Q) return fail(HG_ERR_ARG, "null moments");
+    if (!(g->bc == HG_BC_DIRICHLET_ANALYTIC || g->bc == HG_BC_DIRICHLET_MULTIPOLE))
+        return fail(HG_ERR_STATE, "boundary moments exist only for the Dirichlet modes");
+    const int nq = (g->lmax + 1) * (g->lmax + 1);
+    for (int q = 0; q < kMaxQ; ++q) g->Q[q] = q < nq ? Q[q] : 0.0;
+    g->have_Q = 1;
+    return set_ghosts_dirichlet(g);
 }
 
 int hg_compare(hg_grid* g, const double* phi_P, int on_device, double out[3]) {
@@ -600,6 +681,7 @@ int hg_adjoint_reset(hg_grid* g) {
     HG_RANGE("hg_adjoint_reset");
     int rc = check_grid(g);
     if (rc) return rc;
+    if (g->ziface) return fail(HG_ERR_STATE, "the adjoint is built for whole grids, not for slabs");
     if (!g->adj) {
         // Dirichlet data do not depend on rho in the adjoint: the shadow grid keeps zero boundary data (no density is
         // ever set on it, so its source is zero as well)

@@ -148,6 +148,7 @@ struct hg_grid {
     double mass, rho_bar;
     long long step;
     int tdepth;
+    int ziface;  // bit 0 / bit 1: -z / +z face is an interface to a neighbouring slab (hg_set_z_interface)
     int zb;  // z planes per block of the single sweep (0 = default rule; set by the batch autotuner)
     hg::YlmNorm ylm;
     // measurement: kernel launch count and CUDA events around the sub-step kernel
@@ -234,6 +235,8 @@ struct Bnd {
     int faces;              // 1: Robin ghosts to update (block epilogue)
     int periodic;           // 1: copy the new boundary cells into the opposite ghosts (block epilogue)
     int xfaces;             // 0, or HG_BC_PERIODIC: the x-face ghost copies are made inside the sweep loop
+    int zskip;              // bit 0 / bit 1: the -z / +z face is an interface to a neighbouring slab (its ghost
+                            // plane is supplied by the caller before each sub-step and never written by a sweep)
     const float2* robin32;  // (alpha, beta) per face ghost, compensated float grids
     const double* robin;    // (a = nu/mu, r_g, r_i) per face ghost, FP64 grids
     long long off[7];       // face offsets in the ghost enumeration (hg::Faces)

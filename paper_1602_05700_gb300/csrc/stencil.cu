@@ -355,6 +355,8 @@ __device__ __forceinline__ void ghost_cells(const Layout& L, const Bnd& B, int t
 __global__ void __launch_bounds__(256) k_ghosts_robin(const SweepArgs A, int t0) {
     const int t = t0 + blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= (int)A.B.off[6]) return;
+    if (((A.B.zskip & 1) && t >= (int)A.B.off[4] && t < (int)A.B.off[5]) || ((A.B.zskip & 2) && t >= (int)A.B.off[5]))
+        return;  // a slab interface: the caller supplies that ghost plane
     long long qg, qi, qo;
     ghost_cells(A.L, A.B, t, qg, qi, qo);
     if (A.prec == HG_PREC_F32K) {
@@ -463,6 +465,7 @@ SweepArgs sweep_args(const hg_grid* g, int zb) {
     A.B.faces = g->bc == HG_BC_ROBIN ? 1 : 0;
     A.B.periodic = g->bc == HG_BC_PERIODIC ? 1 : 0;
     A.B.xfaces = 0;
+    A.B.zskip = g->ziface;
     A.B.robin32 = g->robin32;
     A.B.robin = g->robin;
     for (int f = 0; f < 7; ++f) A.B.off[f] = g->F.off[f];

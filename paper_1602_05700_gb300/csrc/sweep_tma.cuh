@@ -282,7 +282,7 @@ __device__ __forceinline__ void tma_sweep(const CUtensorMap* m_hi, const CUtenso
                 lo_n[qg + e] = lo_encode(gh, gl);
             }
     };
-    if (ok && B.faces && k0 == 0 && active) zface(4, hm, lm, hc, lc, q - L.plane);
+    if (ok && B.faces && k0 == 0 && active && !(B.zskip & 1)) zface(4, hm, lm, hc, lc, q - L.plane);
 
     for (int it = 0; it < planes - 1 && ok; ++it) {
         const int sc = it % S, sn = (it + 1) % S;
@@ -318,7 +318,8 @@ __device__ __forceinline__ void tma_sweep(const CUtensorMap* m_hi, const CUtenso
         lc = lp;
         q += L.plane;
     }
-    if (ok && B.faces && k1 == L.nz && active) zface(5, hc, lc, hm, lm, q);  // hc: plane nz, hm: plane nz - 1
+    if (ok && B.faces && k1 == L.nz && active && !(B.zskip & 2))
+        zface(5, hc, lc, hm, lm, q);  // hc: plane nz, hm: plane nz - 1
     if (B.periodic) {  // batched launches: periodic ghosts of the tile's boundary cells, after all consumers stored
         asm volatile("bar.sync 1, %0;" ::"r"(32 * WY) : "memory");
         if (ok)
