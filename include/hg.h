@@ -286,10 +286,12 @@ int hg_moments_noalloc(const void* rho, int dtype, int nx, int ny, int nz, doubl
  * split into slabs of consecutive planes, each an hg_grid of its own (origin shifted by k0 h along z, same h, c_h,
  * G, dt, precision, boundary condition), one per device or process.  Before every sub-step each slab's interface
  * ghost planes must hold the neighbouring slabs' boundary planes of phi^n:
- *   hg_set_z_interface(g, lo, hi)      lo / hi = 1: the -z / +z face is an interface (0: an outer face of the whole
- *                                      grid, updated by the boundary condition as usual).  Robin and Dirichlet
- *                                      boundaries only (HG_ERR_STATE for periodic), temporal depth 1 only (the
- *                                      exchange is per sub-step), no batches, no adjoint.
+ *   hg_init_slab(..., z_interfaces)    hg_init_grid for a slab: bit 0 / bit 1 of z_interfaces make the -z / +z face an
+ *                                      interface (the other faces keep the boundary condition; an interface face
+ *                                      needs no boundary data and is exempt from the Robin stability and geometry
+ *                                      checks).  Robin and Dirichlet boundaries only (HG_ERR_STATE for periodic),
+ *                                      temporal depth 1 only (the exchange is per sub-step), no batches, no adjoint.
+ *   hg_set_z_interface(g, lo, hi)      the same flags on an existing grid (its faces have passed the checks).
  *   hg_plane_bytes(g)                  size of one packed plane: nx*ny doubles (F64), or nx*ny floats followed by nx*ny
  *                                      16-bit compensation codes (F32K).
  *   hg_get_plane(g, which, buf, dev)   copies the first (which = 0, k = 0) or last (which = 1, k = nz-1) interior
@@ -304,6 +306,8 @@ int hg_moments_noalloc(const void* rho, int dtype, int nx, int ny, int nz, doubl
  * With these, k sub-steps of the slabs (exchange, then hg_step(g, 1) on every slab, k times) reproduce k sub-steps of
  * the whole grid bit for bit (Robin; Dirichlet up to the rounding of the summed moments).
  */
+int hg_init_slab(hg_grid** g, int nx, int ny, int nz, double h, const double origin[3], double c_h, double G,
+                 double dt, int precision, int bc, int lmax, void* cuda_stream, int z_interfaces);
 int hg_set_z_interface(hg_grid* g, int lo, int hi);
 size_t hg_plane_bytes(const hg_grid* g);
 int hg_get_plane(hg_grid* g, int which, void* buf, int on_device);

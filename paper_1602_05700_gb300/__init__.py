@@ -87,7 +87,9 @@ def _writable_host(x) -> bool:
 class Grid:
     """One grid of nx*ny*nz cells of side h (lower corner `origin`), wave speed c, constant G, sub-step dt."""
 
-    def __init__(self, nx, ny, nz, h, origin, c, G, dt, precision="f32k", bc="robin", lmax=0, stream=None):
+    def __init__(self, nx, ny, nz, h, origin, c, G, dt, precision="f32k", bc="robin", lmax=0, stream=None,
+                 z_interfaces=0):
+        """z_interfaces (bits 0 / 1): the -z / +z face is an interface to a neighbouring slab (hg_init_slab)."""
         torch = _torch()
         L = _lib.lib()
         if stream is None:
@@ -97,8 +99,13 @@ class Grid:
         org = (ctypes.c_double * 3)(*[float(o) for o in origin])
         prec = PREC[precision] if isinstance(precision, str) else int(precision)
         bcc = BC[bc] if isinstance(bc, str) else int(bc)
-        _lib.check(L.hg_init_grid(ctypes.byref(handle), int(nx), int(ny), int(nz), float(h), org, float(c), float(G),
-                                  float(dt), prec, bcc, int(lmax), ctypes.c_void_p(stream.cuda_stream)))
+        if z_interfaces:
+            _lib.check(L.hg_init_slab(ctypes.byref(handle), int(nx), int(ny), int(nz), float(h), org, float(c),
+                                      float(G), float(dt), prec, bcc, int(lmax), ctypes.c_void_p(stream.cuda_stream),
+                                      int(z_interfaces)))
+        else:
+            _lib.check(L.hg_init_grid(ctypes.byref(handle), int(nx), int(ny), int(nz), float(h), org, float(c),
+                                      float(G), float(dt), prec, bcc, int(lmax), ctypes.c_void_p(stream.cuda_stream)))
         self._h = handle
         self.nx, self.ny, self.nz, self.h = int(nx), int(ny), int(nz), float(h)
         self.origin = tuple(float(o) for o in origin)

@@ -83,6 +83,7 @@ SIGNATURES = {
     "hg_batch_free": (None, [_V]),
     "hg_moments_noalloc": (_I, [_V, _I, _I, _I, _I, _D, _P(_D), _I, _V, _I, _V]),
     "hg_probe_rate": (_I, [_I, _P(_D), _P(_D)]),
+    "hg_init_slab": (_I, [_P(_V), _I, _I, _I, _D, _P(_D), _D, _D, _D, _I, _I, _I, _V, _I]),
     "hg_set_z_interface": (_I, [_V, _I, _I]),
     "hg_plane_bytes": (ctypes.c_size_t, [_V]),
     "hg_get_plane": (_I, [_V, _I, _V, _I]),

@@ -65,6 +65,12 @@ static int build_robin(hg_grid* g) {
     for (long long t = 0; t < n; ++t) {
         int gc[3], ic[3];
         int f = face_cell(g->F, g->nx, g->ny, g->nz, t, gc, ic);
+        if ((f == 4 && (g->ziface & 1)) || (f == 5 && (g->ziface & 2))) {  // a slab interface: never updated
+            c[3 * t] = 0.0;
+            c[3 * t + 1] = 1.0;
+            c[3 * t + 2] = 1.0;
+            continue;
+        }
         double xg[3], xi[3];
         for (int a = 0; a < 3; ++a) {
             xg[a] = g->origin[a] + (gc[a] + 0.5) * g->h;
@@ -181,8 +187,8 @@ extern "C" {
 
 const char* hg_last_error(void) { return g_last_error.c_str(); }
 
-int hg_init_grid(hg_grid** out, int nx, int ny, int nz, double h, const double origin[3], double c_h, double G,
-                 double dt, int precision, int bc, int lmax, void* cuda_stream) {
+static int init_grid(hg_grid** out, int nx, int ny, int nz, double h, const double origin[3], double c_h, double G,
+                     double dt, int precision, int bc, int lmax, void* cuda_stream, int ziface) {
     g_last_error.clear();
     if (!out) return fail(HG_ERR_ARG, "null output pointer");
     *out = nullptr;
@@ -221,6 +227,7 @@ int hg_init_grid(hg_grid** out, int nx, int ny, int nz, double h, const double o
     g->L = make_layout(nx, ny, nz, g->esize);
     g->F = make_faces(nx, ny, nz);
     g->tdepth = 1;
+    g->ziface = ziface;
     fill_ylm_norms(g->ylm);
     int rc = HG_OK;
     cudaError_t e = cudaGetDevice(&g->device);
@@ -230,7 +237,8 @@ int hg_init_grid(hg_grid** out, int nx, int ny, int nz, double h, const double o
     if (rc == HG_OK && (bc == HG_BC_DIRICHLET_ANALYTIC || bc == HG_BC_DIRICHLET_MULTIPOLE)) {
         for (long long t = 0; t < g->F.off[6] && rc == HG_OK; ++t) {
             int gc[3], ic[3];
-            face_cell(g->F, nx, ny, nz, t, gc, ic);
+            const int f = face_cell(g->F, nx, ny, nz, t, gc, ic);
+            if ((f == 4 && (ziface & 1)) || (f == 5 && (ziface & 2))) continue;  // a slab interface: no boundary data
             double r2 = 0.0;
             for (int a = 0; a < 3; ++a) {
                 double x = origin[a] + (gc[a] + 0.5) * h;
@@ -292,6 +300,22 @@ static int set_density_device(hg_grid* g, const void* src, int dtype) {
         if ((rc = set_ghosts_dirichlet(g))) return rc;
     }
     return HG_OK;
+}
+
+int hg_init_grid(hg_grid** out, int nx, int ny, int nz, double h, const double origin[3], double c_h, double G,
+                 double dt, int precision, int bc, int lmax, void* cuda_stream) {
+    HG_RANGE("hg_init_grid");
+    return init_grid(out, nx, ny, nz, h, origin, c_h, G, dt, precision, bc, lmax, cuda_stream, 0);
+}
+
+int hg_init_slab(hg_grid** out, int nx, int ny, int nz, double h, const double origin[3], double c_h, double G,
+                 double dt, int precision, int bc, int lmax, void* cuda_stream, int z_interfaces) {
+    HG_RANGE("hg_init_slab");
+    if (z_interfaces < 0 || z_interfaces > 3) return fail(HG_ERR_ARG, "z_interfaces must be 0..3");
+    if (z_interfaces && bc == HG_BC_PERIODIC)
+        return fail(HG_ERR_STATE, "slab interfaces are built for the Robin and Dirichlet boundaries (a periodic "
+                                  "source needs the mean density of the whole grid)");
+    return init_grid(out, nx, ny, nz, h, origin, c_h, G, dt, precision, bc, lmax, cuda_stream, z_interfaces);
 }
 
 int hg_set_density(hg_grid* g, const void* rho, int dtype, int on_device) {

@@ -51,9 +51,9 @@ class GridSlab:
 
         self.k0, self.k1, self.index, self.parts = int(k0), int(k1), int(index), int(parts)
         o = (float(origin[0]), float(origin[1]), float(origin[2]) + self.k0 * float(h))
-        self.grid = Grid(nx, ny, self.k1 - self.k0, h, o, c, G, dt, precision, bc, lmax, stream)
         self.lo, self.hi = self.index > 0, self.index < self.parts - 1
-        _lib.check(_lib.lib().hg_set_z_interface(self.grid.handle, int(self.lo), int(self.hi)))
+        self.grid = Grid(nx, ny, self.k1 - self.k0, h, o, c, G, dt, precision, bc, lmax, stream,
+                         z_interfaces=(1 if self.lo else 0) | (2 if self.hi else 0))
         self.nbytes = int(_lib.lib().hg_plane_bytes(self.grid.handle))
 
     def plane_buffer(self, device=None):

@@ -25,7 +25,7 @@ from paper_1602_05700_gb300 import slab as S  # noqa: E402
 
 NX, NY, NZ, STEPS, LMAX = 64, 57, 61, 40, 3
 H = 1.0 / 64
-ORIGIN = (-0.5, -0.45, -0.48)
+ORIGIN = (-0.5, -0.4375, -0.46875)  # on the grid of h = 1/64: every cell coordinate is exact
 DT = 0.5 * H / np.sqrt(3.0)
 
 
