@@ -9,11 +9,15 @@
 // while the grids' states move on.  Results are identical to stepping each grid on its own: the per-cell arithmetic
 // is the same code.
 //
-// Autotuning: the z extent of an FP64 block (planes per block, which sets the number of blocks and the share of
-// the z warm-up) is chosen from a few candidates by timing the first sub-steps of the first hg_batch_step with
+// Autotuning: three knobs of the launch are chosen by timing the first sub-steps of the first hg_batch_step with
 // CUDA events -- every candidate computes the same result, so the timing runs are real sub-steps -- and cached per
-// (device, set of grid shapes/precisions/boundaries) for the process.  The TMA-staged blocks of the compensated-float
-// grids use 8 planes, where their stage ring hides the z warm-up.
+// (device, set of grid shapes/precisions/boundaries) for the process:
+//   * the tile shape of an FP64 block: rows of 128 cells (4 per lane) for every grid, or per grid whichever of
+//     128- and 32-cell rows (1 per lane) leaves fewer lanes idle (a 96-cell row fills 75% of a 128-cell tile; the
+//     FP64 pipe pays for idle lanes, since its rate is per warp instruction);
+//   * the z extent of an FP64 block (8 .. 64 planes: the number of blocks against the share of the z warm-up);
+//   * the z extent of a TMA-staged compensated-float block (8 or 16 planes).
+// All FP64 candidates are timed first (eight), then the two float extents with the best FP64 setting.
 #include <stdio.h>
 #include <string.h>
 
@@ -37,7 +41,9 @@ struct hg_batch {
     unsigned* d_first;
     unsigned total_blocks;
     std::vector<unsigned> first;
-    int zb;  // planes per block, 0 until tuned
+    int zb;    // FP64 planes per block, 0 until tuned
+    int cpl;   // FP64 cells per lane: 0 = per grid, whichever tile row fits better; 4 = 128-cell rows everywhere
+    int zb32;  // compensated-float (TMA-staged) planes per block
     // graph of `graph_steps` sub-steps
     cudaGraph_t graph;
     cudaGraphExec_t exec;
@@ -47,7 +53,10 @@ struct hg_batch {
 namespace {
 
 std::mutex g_tune_mu;
-std::map<std::string, int> g_tuned;  // autotuner cache: key -> planes per block
+struct Tuning {
+    int zb, cpl, zb32;
+};
+std::map<std::string, Tuning> g_tuned;  // autotuner cache: key -> the chosen launch
 
 std::string tune_key(const hg_batch* b) {
     cudaDeviceProp p;
@@ -75,9 +84,9 @@ int upload_tables(hg_batch* b) {
             memset(&e, 0, sizeof e);
             int rc = HG_OK;
             if (g->prec == HG_PREC_F32K) {
-                rc = tma_entry(g, &e);  // TMA-staged blocks: a fixed 8-plane chunk
+                rc = tma_entry(g, &e, b->zb32);
             } else {
-                e.A = sweep_args(g, b->zb);
+                e.A = sweep_args(g, b->zb, b->cpl);
                 e.err = g->derr;
             }
             g->cur = cur;
@@ -107,8 +116,8 @@ void advance(hg_batch* b, int n) {
     }
 }
 
-// pick the planes per block by timing two sub-steps per candidate (real sub-steps: every candidate gives the same
-// result); returns the number of sub-steps taken
+// pick the launch by timing two sub-steps per candidate (real sub-steps: every candidate gives the same result);
+// returns the number of sub-steps taken in *taken
 int autotune(hg_batch* b, int budget, int* taken) {
     *taken = 0;
     const std::string key = tune_key(b);
@@ -116,52 +125,78 @@ int autotune(hg_batch* b, int budget, int* taken) {
         std::lock_guard<std::mutex> lock(g_tune_mu);
         auto it = g_tuned.find(key);
         if (it != g_tuned.end()) {
-            b->zb = it->second;
+            b->zb = it->second.zb;
+            b->cpl = it->second.cpl;
+            b->zb32 = it->second.zb32;
             return upload_tables(b);
         }
     }
-    bool any64 = false;
-    for (hg_grid* g : b->grids) any64 = any64 || g->prec == HG_PREC_F64;
-    if (!any64) {  // nothing to tune: the TMA-staged blocks use a fixed chunk
-        b->zb = 8;
-        return upload_tables(b);
+    bool any64 = false, any32 = false;
+    for (hg_grid* g : b->grids) {
+        any64 = any64 || g->prec == HG_PREC_F64;
+        any32 = any32 || g->prec == HG_PREC_F32K;
     }
-    const int cand[] = {8, 16, 32, 64};
-    int best = 0;
-    float best_ms = 0.f;
+    std::vector<Tuning> cand;
+    if (any64)
+        for (int cpl : {0, 4})
+            for (int zb : {8, 16, 32, 64}) cand.push_back({zb, cpl, 8});
+    else
+        cand.push_back({8, 0, 8});
+    Tuning best = cand[0];
+    float best_ms = -1.f;
     cudaEvent_t e0, e1;
     HG_CUDA(cudaEventCreate(&e0));
     HG_CUDA(cudaEventCreate(&e1));
     int rc = HG_OK;
-    for (int c : cand) {
-        if (*taken >= budget) break;
-        if (*taken + 2 > budget) break;
-        b->zb = c;
-        if ((rc = upload_tables(b))) break;
+    bool complete = true;
+    auto time_one = [&](const Tuning& t) -> bool {  // false: no budget left or an error (rc)
+        if (*taken + 2 > budget) {
+            complete = false;
+            return false;
+        }
+        b->zb = t.zb;
+        b->cpl = t.cpl;
+        b->zb32 = t.zb32;
+        if ((rc = upload_tables(b))) return false;
         cudaEventRecord(e0, b->stream);
-        if ((rc = enqueue_substep(b, 0))) break;  // two sub-steps (both parities) per candidate
-        if ((rc = enqueue_substep(b, 1))) break;
+        if ((rc = enqueue_substep(b, 0))) return false;  // two sub-steps (both parities) per candidate
+        if ((rc = enqueue_substep(b, 1))) return false;
         cudaEventRecord(e1, b->stream);
         cudaError_t e = cudaEventSynchronize(e1);
         if (e != cudaSuccess) {
             rc = cuda_fail(e, "autotuner timing");
-            break;
+            return false;
         }
         float ms = 0.f;
         cudaEventElapsedTime(&ms, e0, e1);
         advance(b, 2);
         *taken += 2;
-        if (best == 0 || ms < best_ms) {
-            best = c;
+        if (best_ms < 0.f || ms < best_ms) {
+            best = t;
             best_ms = ms;
         }
+        return true;
+    };
+    for (const Tuning& t : cand)
+        if (!time_one(t)) break;
+    if (rc == HG_OK && complete && any32 && best_ms >= 0.f) {
+        Tuning t = best;
+        t.zb32 = 16;
+        time_one(t);
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (rc) return rc;
-    if (best == 0) return HG_OK;  // no budget to tune: keep the default rule this time
-    b->zb = best;
-    if (*taken == 2 * (int)(sizeof cand / sizeof cand[0])) {
+    if (best_ms < 0.f) {  // no budget to tune: the default launch this time
+        b->zb = 8;
+        b->cpl = 0;
+        b->zb32 = 8;
+        return upload_tables(b);
+    }
+    b->zb = best.zb;
+    b->cpl = best.cpl;
+    b->zb32 = best.zb32;
+    if (complete) {
         std::lock_guard<std::mutex> lock(g_tune_mu);
         g_tuned[key] = best;
     }
@@ -277,6 +312,15 @@ int hg_batch_info(const hg_batch* b, int* z_planes_per_block, long long* blocks_
     if (!b) return fail(HG_ERR_ARG, "null batch");
     if (z_planes_per_block) *z_planes_per_block = b->zb;
     if (blocks_per_substep) *blocks_per_substep = b->total_blocks;
+    return HG_OK;
+}
+
+int hg_batch_tuning(const hg_batch* b, int out[3]) {
+    HG_RANGE("hg_batch_tuning");
+    if (!b || !out) return fail(HG_ERR_ARG, "null argument");
+    out[0] = b->zb;
+    out[1] = b->cpl;
+    out[2] = b->zb32;
     return HG_OK;
 }
 

@@ -26,10 +26,17 @@ __device__ __forceinline__ float lo_decode(float hi, lo_t f) {
     return __fmul_rn(hi, __fmul_rn(__half2float(f), 5.9604644775390625e-8f));  // f * 2^-24 is exact
 }
 
-// f = 2^24 lo / hi by the approximate reciprocal (the code only has to be decoded consistently); lo = 0 whenever
-// hi = 0 (a Fast2Sum with a zero sum has a zero error), which the select keeps away from 0 * inf
+// f = 2^24 lo / hi with the hardware's approximate reciprocal (rcp.approx: the code only has to be decoded
+// consistently, so its last bits need no correct rounding); lo = 0 whenever hi = 0 (a Fast2Sum with a zero sum has a
+// zero error), which the select keeps away from 0 * inf.  A nonzero lo never comes with a subnormal hi (a sum that
+// rounds to a subnormal is exact), so |f| <= 1 (1 + 2^-22 with the approximate reciprocal).
+__device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
 __device__ __forceinline__ lo_t lo_encode(float hi, float lo) {
-    const float f = lo == 0.f ? 0.f : __fdividef(__fmul_rn(lo, 16777216.f), hi);
+    const float f = lo == 0.f ? 0.f : __fmul_rn(__fmul_rn(lo, 16777216.f), rcp_approx(hi));
     return __float2half_rn(f);
 }
 
@@ -37,22 +44,41 @@ __device__ __forceinline__ lo_t lo_encode(float hi, float lo) {
 // round exactly like the single sweep)
 __device__ __forceinline__ float lo_round(float hi, float lo) { return lo_decode(hi, lo_encode(hi, lo)); }
 
+// ---- packed pairs ---------------------------------------------------------------------------------------------
+// sm_100 and later round two float operations in one instruction (add.f32x2, mul.f32x2, fma.f32x2), each exactly as
+// the scalar operation would: the four-cell helpers below give the bits of four scalar calls in fewer instructions.
+__device__ __forceinline__ float2 pa(const float4& v) { return make_float2(v.x, v.y); }  // cells 0, 1 of a group
+__device__ __forceinline__ float2 pb(const float4& v) { return make_float2(v.z, v.w); }  // cells 2, 3
+__device__ __forceinline__ float4 join4(float2 a, float2 b) { return make_float4(a.x, a.y, b.x, b.y); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 dup2(float a) { return make_float2(a, a); }
+
 // four consecutive codes as one 8-byte word
 __device__ __forceinline__ float4 lo_decode4(const float4& hi, uint2 raw) {
     const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&raw.x));
     const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&raw.y));
-    const float k = 5.9604644775390625e-8f;
-    return make_float4(__fmul_rn(hi.x, __fmul_rn(a.x, k)), __fmul_rn(hi.y, __fmul_rn(a.y, k)),
-                       __fmul_rn(hi.z, __fmul_rn(b.x, k)), __fmul_rn(hi.w, __fmul_rn(b.y, k)));
+    const float2 k = dup2(5.9604644775390625e-8f);
+    return join4(mul2(pa(hi), mul2(a, k)), mul2(pb(hi), mul2(b, k)));
 }
 __device__ __forceinline__ uint2 lo_encode4(const float4& hi, const float4& lo) {
-    const lo_t c0 = lo_encode(hi.x, lo.x), c1 = lo_encode(hi.y, lo.y), c2 = lo_encode(hi.z, lo.z),
-               c3 = lo_encode(hi.w, lo.w);
+    const float2 k = dup2(16777216.f);
+    float2 fa = mul2(mul2(pa(lo), k), make_float2(rcp_approx(hi.x), rcp_approx(hi.y)));
+    float2 fb = mul2(mul2(pb(lo), k), make_float2(rcp_approx(hi.z), rcp_approx(hi.w)));
+    fa.x = lo.x == 0.f ? 0.f : fa.x;
+    fa.y = lo.y == 0.f ? 0.f : fa.y;
+    fb.x = lo.z == 0.f ? 0.f : fb.x;
+    fb.y = lo.w == 0.f ? 0.f : fb.y;
+    const __half2 ha = __floats2half2_rn(fa.x, fa.y), hb = __floats2half2_rn(fb.x, fb.y);
     uint2 r;
-    r.x = (unsigned)__half_as_ushort(c0) | ((unsigned)__half_as_ushort(c1) << 16);
-    r.y = (unsigned)__half_as_ushort(c2) | ((unsigned)__half_as_ushort(c3) << 16);
+    r.x = *reinterpret_cast<const unsigned*>(&ha);
+    r.y = *reinterpret_cast<const unsigned*>(&hb);
     return r;
 }
+// lo after a store and a load, for four cells
+__device__ __forceinline__ float4 lo_round4(const float4& hi, const float4& lo) { return lo_decode4(hi, lo_encode4(hi, lo)); }
 
 // f32 with compensated increments: phi^n = hi + lo, d = phi^n - phi^{n-1}.
 //   L  = sum(hi_nb - hi) + sum(lo_nb) - 6 lo          (neighbour order -x, +x, -y, +y, -z, +z)
@@ -75,6 +101,43 @@ __device__ __forceinline__ void f32k_update(float xl, float xr, float ys, float 
     lo_o = __fsub_rn(y, __fsub_rn(t, c));
     hi_o = t;
     d_o = dn;
+}
+
+// The same sub-step for a group of four consecutive cells of a row (c, lc; x neighbours xl, lxl before the group
+// and xr, lxr after it), giving the bits of four f32k_update calls.  The x differences are shared between neighbouring
+// cells: with D_e = c_{e+1} - c_e rounded (c_{-1} = xl, c_4 = xr), RN(c_{e-1} - c_e) = -D_{e-1} exactly, so the first
+// partial sum (xl - c) + (xr - c) of cell e is RN(D_e - D_{e-1}); everything after it runs on packed pairs.
+__device__ __forceinline__ void f32k_update4(const float4& c, const float4& lc, float xl, float lxl, float xr,
+                                             float lxr, const float4& ys, const float4& yn, const float4& zm,
+                                             const float4& zp, const float4& lys, const float4& lyn, const float4& lzm,
+                                             const float4& lzp, const float4& d, const float4& s, float nu2,
+                                             float4& ho, float4& lo, float4& dout) {
+    const float Dm = __fsub_rn(c.x, xl), D0 = __fsub_rn(c.y, c.x), D1 = __fsub_rn(c.z, c.y), D2 = __fsub_rn(c.w, c.z),
+                D3 = __fsub_rn(xr, c.w);
+    const float2 n2 = dup2(nu2);
+    // one pair after the other (cells 0, 1 then 2, 3), which keeps fewer values live at once
+    auto pair = [&](float2 A, float2 L, float2 cc, float2 vys, float2 vyn, float2 vzm, float2 vzp, float2 lsy,
+                    float2 lny, float2 lzmm, float2 lzpp, float2 lcc, float2 dd, float2 ss, float2& h2, float2& l2,
+                    float2& d2) {
+        A = add2(A, sub2(vys, cc));
+        A = add2(A, sub2(vyn, cc));
+        A = add2(A, sub2(vzm, cc));
+        A = add2(A, sub2(vzp, cc));
+        L = add2(add2(L, add2(lsy, lny)), add2(lzmm, lzpp));
+        L = fma2(dup2(-6.0f), lcc, L);
+        d2 = add2(dd, fma2(n2, add2(A, L), make_float2(-ss.x, -ss.y)));
+        const float2 y = add2(d2, lcc);
+        h2 = add2(cc, y);
+        l2 = sub2(y, sub2(h2, cc));
+    };
+    float2 ha, la, da, hb, lb, db;
+    pair(make_float2(__fsub_rn(D0, Dm), __fsub_rn(D1, D0)), make_float2(__fadd_rn(lxl, lc.y), __fadd_rn(lc.x, lc.z)),
+         pa(c), pa(ys), pa(yn), pa(zm), pa(zp), pa(lys), pa(lyn), pa(lzm), pa(lzp), pa(lc), pa(d), pa(s), ha, la, da);
+    pair(make_float2(__fsub_rn(D2, D1), __fsub_rn(D3, D2)), make_float2(__fadd_rn(lc.y, lc.w), __fadd_rn(lc.z, lxr)),
+         pb(c), pb(ys), pb(yn), pb(zm), pb(zp), pb(lys), pb(lyn), pb(lzm), pb(lzp), pb(lc), pb(d), pb(s), hb, lb, db);
+    ho = join4(ha, hb);
+    lo = join4(la, lb);
+    dout = join4(da, db);
 }
 
 // f64: phi^{n+1} = ((2c - prev) + nu^2 L) - s with L = (((((xl-c) + (xr-c)) + (ys-c)) + (yn-c)) + (zm-c)) + (zp-c):
@@ -122,7 +185,8 @@ __device__ __forceinline__ void robin_update_f32k(float a, float b, float hg, fl
 // a double as a float and the code of its rounding remainder, and back
 __device__ __forceinline__ void split_f32(double v, float& hi, lo_t& lo) {
     hi = __double2float_rn(v);
-    lo = lo_encode(hi, __double2float_rn(__dsub_rn(v, (double)hi)));
+    // a subnormal (or zero) hi keeps no compensation: its remainder is below 2^-149 and has no code
+    lo = lo_encode(hi, fabsf(hi) < 1.17549435e-38f ? 0.f : __double2float_rn(__dsub_rn(v, (double)hi)));
 }
 __device__ __forceinline__ double join_f32(float hi, lo_t lo) {
     return __dadd_rn((double)hi, (double)lo_decode(hi, lo));

@@ -128,6 +128,8 @@ int smem_attr_once(const void* fn, int bytes, unsigned long long* done) {
     const unsigned long long bit = 1ull << (dev & 63);
     if (*done & bit) return HG_OK;
     HG_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    // the whole unified L1 / shared array as shared memory, so that the blocks the registers allow also fit
+    HG_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared));
     *done |= bit;
     return HG_OK;
 }

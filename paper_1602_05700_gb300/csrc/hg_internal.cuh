@@ -255,11 +255,14 @@ struct SweepArgs {
     float nu2f;        // nu^2 rounded to float once (compensated float sweeps)
     int zb;            // z planes per block
     int prec;
+    int cpl;           // FP64 sweep: x cells per lane (4: 128-cell tile rows; 1: 32-cell rows, for nx that 128 fits badly)
     unsigned gx, gy;   // blocks in x and y of this grid's sweep
     Bnd B;
 };
 
-SweepArgs sweep_args(const hg_grid* g, int zb);  // sub-step cur -> 1 - cur of grid g; zb = 0: default z chunk
+SweepArgs sweep_args(const hg_grid* g, int zb, int cpl = 0);  // sub-step cur -> 1 - cur of grid g; zb = 0: default z
+                                                              // chunk; cpl = 0: FP64 cells per lane by tile fit
+int f64_cells_per_lane(int nx);  // 4, or 1 when 32-cell tile rows waste fewer lanes than 128-cell ones
 // a 3-D TMA map over a padded array (pitch x (ny+2) x (nz+2) elements of `bytes` each), boxes box_x x box_y x 1
 int tma_encode(CUtensorMap* m, void* base, const Layout& L, int bytes, int box_x, int box_y);
 
@@ -270,7 +273,7 @@ struct alignas(128) TmaEntry {
     SweepArgs A;
     int* err;
 };
-int tma_entry(hg_grid* g, TmaEntry* e);  // compensated-float g's sub-step cur -> 1 - cur (all ghosts in the launch)
+int tma_entry(hg_grid* g, TmaEntry* e, int zb = 0);  // compensated-float g's sub-step cur -> 1 - cur (all ghosts in the launch)
 int launch_step_batch(cudaStream_t st, const TmaEntry* tab, const unsigned* first, int n, unsigned total_blocks);
 unsigned sweep_blocks(const SweepArgs& A);
 

@@ -74,9 +74,9 @@ __device__ __forceinline__ void batched(int count, int tid, int nth, Where&& whe
 
 template <class Upd>
 __device__ __forceinline__ void block_face_ghosts(const Layout& L, const Bnd& B, int x0, int j0, int wy, int k0, int k1,
-                                                  int bx, int by, int gx, int gy, Upd&& upd) {
+                                                  int bx, int by, int gx, int gy, Upd&& upd, int tw = 128) {
     const int tid = threadIdx.y * blockDim.x + threadIdx.x, nth = blockDim.x * blockDim.y;
-    const int jn = min(wy, L.ny - j0), xn = min(128, L.nx - x0), kn = k1 - k0;
+    const int jn = min(wy, L.ny - j0), xn = min(tw, L.nx - x0), kn = k1 - k0;
     if (bx == 0)
         batched(jn * kn, tid, nth, [&](int t, long long& qg, long long& qi, long long& r) {
             const int j = j0 + t % jn, k = k0 + t / jn;
@@ -212,31 +212,30 @@ __device__ __forceinline__ void sweep_f32k(const SweepArgs& A, int bx, int by, i
     }
 }
 
-// f64: 4 cells per lane as two double2 (arithmetic in cell.cuh)
-struct D4 {
-    double v[4];
+// f64: C = 4 cells per lane (two double2 accesses) or C = 1 (one double); arithmetic in cell.cuh
+template <int C>
+struct DC {
+    double v[C];
 };
-__device__ __forceinline__ D4 ldd4(const double* p) {
-    double2 a = ld2(p), b = ld2(p + 2);
-    D4 r;
-    r.v[0] = a.x;
-    r.v[1] = a.y;
-    r.v[2] = b.x;
-    r.v[3] = b.y;
-    return r;
-}
-__device__ __forceinline__ D4 ldd4rw(const double* p) {
-    double2 a = ld2rw(p), b = ld2rw(p + 2);
-    D4 r;
-    r.v[0] = a.x;
-    r.v[1] = a.y;
-    r.v[2] = b.x;
-    r.v[3] = b.y;
+template <int C>
+__device__ __forceinline__ DC<C> ldd(const double* p, bool ro) {
+    DC<C> r;
+    if constexpr (C == 4) {
+        const double2 a = ro ? ld2(p) : ld2rw(p), b = ro ? ld2(p + 2) : ld2rw(p + 2);
+        r.v[0] = a.x;
+        r.v[1] = a.y;
+        r.v[2] = b.x;
+        r.v[3] = b.y;
+    } else {
+        r.v[0] = ro ? __ldg(p) : *p;
+    }
     return r;
 }
 
-template <int WY>
+// The FP64 sweep of tile (bx, by) and z chunk bz: a warp owns a row of 32 C cells (C per lane).
+template <int WY, int C>
 __device__ __forceinline__ void sweep_f64(const SweepArgs& A, int bx, int by, int bz) {
+    constexpr int TW = 32 * C;
     const double* __restrict__ phi_c = (const double*)A.hi_c;
     double* __restrict__ phi_pn = (double*)A.hi_n;
     const double* __restrict__ rho = (const double*)A.rho;
@@ -246,52 +245,52 @@ __device__ __forceinline__ void sweep_f64(const SweepArgs& A, int bx, int by, in
     const int zb = A.zb;
     const int lane = threadIdx.x;
     const int j = by * WY + threadIdx.y;
-    const int i0 = bx * 128 + lane * 4;
+    const int i0 = bx * TW + lane * C;
     const bool active = i0 < L.nx;  // this lane owns cells
     const bool halo = i0 <= L.nx;   // this lane's group holds cells or the +x ghost
-    const bool full = i0 + 3 < L.nx;
+    const bool full = i0 + C - 1 < L.nx;
     const int k0 = bz * zb;
     const int k1 = min(L.nz, k0 + zb);
-    D4 zero;
+    DC<C> zero;
 #pragma unroll
-    for (int e = 0; e < 4; ++e) zero.v[e] = 0.0;
+    for (int e = 0; e < C; ++e) zero.v[e] = 0.0;
     if (j < L.ny && (int)threadIdx.y < WY) {  // rows past ny (or extra warps) only join the epilogue
     long long q = L.at(i0, j, k0);
-    D4 cm = zero, cc = zero;
+    DC<C> cm = zero, cc = zero;
     if (halo) {
-        cm = ldd4(phi_c + q - L.plane);
-        cc = ldd4(phi_c + q);
+        cm = ldd<C>(phi_c + q - L.plane, true);
+        cc = ldd<C>(phi_c + q, true);
     }
     for (int k = k0; k < k1; ++k, q += L.plane) {
-        D4 cp = zero, ys = zero, yn = zero, pv = zero, r = zero;
+        DC<C> cp = zero, ys = zero, yn = zero, pv = zero, r = zero;
         double xl = 0.0, xr = 0.0;
-        if (halo) cp = ldd4(phi_c + q + L.plane);
+        if (halo) cp = ldd<C>(phi_c + q + L.plane, true);
         if (active) {
-            ys = ldd4(phi_c + q - L.pitch);
-            yn = ldd4(phi_c + q + L.pitch);
-            pv = ldd4rw(phi_pn + q);
-            r = ldd4(rho + q);
+            ys = ldd<C>(phi_c + q - L.pitch, true);
+            yn = ldd<C>(phi_c + q + L.pitch, true);
+            pv = ldd<C>(phi_pn + q, false);
+            r = ldd<C>(rho + q, true);
             if (lane == 0) xl = __ldg(phi_c + q - 1);
-            if (lane == 31 && i0 + 4 <= L.nx) xr = __ldg(phi_c + q + 4);
+            if (lane == 31 && i0 + C <= L.nx) xr = __ldg(phi_c + q + C);
         }
-        double sl = __shfl_up_sync(0xffffffffu, cc.v[3], 1);
+        double sl = __shfl_up_sync(0xffffffffu, cc.v[C - 1], 1);
         double sr = __shfl_down_sync(0xffffffffu, cc.v[0], 1);
         if (lane != 0) xl = sl;
         if (lane != 31) xr = sr;
         if (active) {
-            D4 o;
+            DC<C> o;
 #pragma unroll
-            for (int e = 0; e < 4; ++e) {
+            for (int e = 0; e < C; ++e) {
                 double l = e == 0 ? xl : cc.v[e - 1];
-                double rr = e == 3 ? xr : cc.v[e + 1];
+                double rr = e == C - 1 ? xr : cc.v[e + 1];
                 o.v[e] = f64_update(l, rr, ys.v[e], yn.v[e], cm.v[e], cp.v[e], cc.v[e], pv.v[e], r.v[e], nu2);
             }
-            if (full) {
+            if (C == 4 && full) {
                 st2(phi_pn + q, make_double2(o.v[0], o.v[1]));
-                st2(phi_pn + q + 2, make_double2(o.v[2], o.v[3]));
+                st2(phi_pn + q + 2, make_double2(o.v[C > 2 ? 2 : 0], o.v[C > 3 ? 3 : 0]));
             } else {
 #pragma unroll
-                for (int e = 0; e < 4; ++e)
+                for (int e = 0; e < C; ++e)
                     if (i0 + e < L.nx) phi_pn[q + e] = o.v[e];
             }
         }
@@ -300,7 +299,7 @@ __device__ __forceinline__ void sweep_f64(const SweepArgs& A, int bx, int by, in
     }
     }
     if (B.faces)
-        block_face_ghosts(L, B, bx * 128, by * WY, WY, k0, k1, bx, by, A.gx, A.gy, [&](const GhostBatch& gb) {
+        block_face_ghosts(L, B, bx * TW, by * WY, WY, k0, k1, bx, by, A.gx, A.gy, [&](const GhostBatch& gb) {
             double a[kGB], rg[kGB], ri[kGB], pg[kGB], pi[kGB];
 #pragma unroll
             for (int u = 0; u < kGB; ++u)
@@ -314,12 +313,20 @@ __device__ __forceinline__ void sweep_f64(const SweepArgs& A, int bx, int by, in
 #pragma unroll
             for (int u = 0; u < kGB; ++u)
                 if (u < gb.n) phi_pn[gb.qg[u]] = robin_update_f64(a[u], rg[u], ri[u], pg[u], pi[u]);
-        });
+        }, TW);
     if (B.periodic) {
         __syncthreads();
-        block_periodic_copies(L, bx * 128, by * WY, WY, k0, k1, bx, by, A.gx, A.gy, block_tid(), block_nth(),
-                              [&](long long q, long long d) { phi_pn[d] = phi_pn[q]; });
+        block_periodic_copies(L, bx * TW, by * WY, WY, k0, k1, bx, by, A.gx, A.gy, block_tid(), block_nth(),
+                              [&](long long q, long long d) { phi_pn[d] = phi_pn[q]; }, TW);
     }
+}
+
+template <int WY>
+__device__ __forceinline__ void sweep_f64_any(const SweepArgs& A, int bx, int by, int bz) {
+    if (A.cpl == 1)
+        sweep_f64<WY, 1>(A, bx, by, bz);
+    else
+        sweep_f64<WY, 4>(A, bx, by, bz);
 }
 
 constexpr int kWY = 8;
@@ -408,7 +415,7 @@ int zchunk(const hg_grid* g) {
 
 template <int WY>
 __global__ void __launch_bounds__(32 * WY, 2) k_step_f64(const SweepArgs A) {
-    sweep_f64<WY>(A, blockIdx.x, blockIdx.y, blockIdx.z);
+    sweep_f64_any<WY>(A, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
 // One launch for the sub-step of many grids: block b belongs to the entry e with first[e] <= b < first[e+1]
@@ -439,14 +446,19 @@ __global__ void __launch_bounds__(32 * (WY + 1), 2) k_step_batch(const TmaEntry*
                 asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&E.m[m]) : "memory");
         tma_sweep<WY, S>(&E.m[0], &E.m[1], &E.m[2], &E.m[3], E.A, bx, by, bz, E.err, smem, bars);
     } else {
-        sweep_f64<WY>(E.A, bx, by, bz);
+        sweep_f64_any<WY>(E.A, bx, by, bz);
     }
 }
 
 }  // namespace
 
 // the sweep arguments of grid g for the sub-step cur -> 1 - cur, with z chunks of zb planes (0 = default rule)
-SweepArgs sweep_args(const hg_grid* g, int zb) {
+int f64_cells_per_lane(int nx) {
+    const long long w4 = (nx + 127) / 128 * 128LL, w1 = (nx + 31) / 32 * 32LL;
+    return w1 < w4 ? 1 : 4;
+}
+
+SweepArgs sweep_args(const hg_grid* g, int zb, int cpl) {
     SweepArgs A;
     const int nxt = 1 - g->cur;
     A.hi_c = g->phi[g->cur];
@@ -460,7 +472,8 @@ SweepArgs sweep_args(const hg_grid* g, int zb) {
     A.nu2f = (float)g->nu2;
     A.zb = zb > 0 ? (zb < g->nz ? zb : g->nz) : zchunk(g);
     A.prec = g->prec;
-    A.gx = (g->nx + 127) / 128;
+    A.cpl = g->prec == HG_PREC_F64 ? (cpl > 0 ? cpl : f64_cells_per_lane(g->nx)) : 4;
+    A.gx = (g->nx + 32 * A.cpl - 1) / (32 * A.cpl);
     A.gy = (g->ny + kWY - 1) / kWY;
     A.B.faces = g->bc == HG_BC_ROBIN ? 1 : 0;
     A.B.periodic = g->bc == HG_BC_PERIODIC ? 1 : 0;

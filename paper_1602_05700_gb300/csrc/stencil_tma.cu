@@ -104,7 +104,7 @@ int launch_sweep_f32k_tma(hg_grid* g, const SweepArgs& A) {
 
 // the batched-launch entry of grid g for its sub-step cur -> 1 - cur: Robin ghosts of all faces inside the launch,
 // periodic ghosts by the blocks' epilogue
-int tma_entry(hg_grid* g, TmaEntry* e) {
+int tma_entry(hg_grid* g, TmaEntry* e, int zb) {
     int rc = tma_maps(g);
     if (rc) return rc;
     const int c = g->cur;
@@ -112,7 +112,7 @@ int tma_entry(hg_grid* g, TmaEntry* e) {
     e->m[1] = g->tm[2 + c];
     e->m[2] = g->tm[4 + g->dcur];
     e->m[3] = g->tm[6];
-    e->A = sweep_args(g, 0);
+    e->A = sweep_args(g, zb);
     e->A.gx = (g->nx + kTX - 1) / kTX;
     e->A.gy = (g->ny + kTmaWY - 1) / kTmaWY;
     e->A.B.xfaces = 0;

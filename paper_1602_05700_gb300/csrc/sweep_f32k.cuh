@@ -25,19 +25,7 @@ __device__ __forceinline__ void group_update_store(const Layout& L, const Bnd& B
                                                    const float4& d, const float4& r, float* __restrict__ hi_n,
                                                    lo_t* __restrict__ lo_n, float* __restrict__ dlt) {
     float4 ho, lo, dout;
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-        const float xl = e == 0 ? hl : el(hc, e - 1);
-        const float xr = e == 3 ? hr : el(hc, e + 1);
-        const float lxl = e == 0 ? ll : el(lc, e - 1);
-        const float lxr = e == 3 ? lr : el(lc, e + 1);
-        float a, b, c;
-        f32k_update(xl, xr, el(hs, e), el(hn, e), el(hm, e), el(hp, e), el(hc, e), lxl, lxr, el(ls, e), el(ln, e),
-                    el(lm, e), el(lp, e), el(lc, e), el(d, e), el(r, e), nu2, a, b, c);
-        set(ho, e, a);
-        set(lo, e, b);
-        set(dout, e, c);
-    }
+    f32k_update4(hc, lc, hl, ll, hr, lr, hs, hn, hm, hp, ls, ln, lm, lp, d, r, nu2, ho, lo, dout);
     if (i0 + 3 < L.nx) {
         *reinterpret_cast<float4*>(hi_n + q) = ho;
         *reinterpret_cast<uint2*>(lo_n + q) = lo_encode4(ho, lo);
@@ -74,8 +62,9 @@ __device__ __forceinline__ int block_nth() { return blockDim.x * blockDim.y; }
 // threads tid = 0 .. nth-1.  copy(src, dst) takes padded indices; each boundary cell belongs to exactly one block.
 template <class Copy>
 __device__ __forceinline__ void block_periodic_copies(const Layout& L, int x0, int j0, int wy, int k0, int k1, int bx,
-                                                      int by, int gx, int gy, int tid, int nth, Copy&& copy) {
-    const int jn = min(wy, L.ny - j0), xn = min(128, L.nx - x0), kn = k1 - k0;
+                                                      int by, int gx, int gy, int tid, int nth, Copy&& copy,
+                                                      int tw = 128) {
+    const int jn = min(wy, L.ny - j0), xn = min(tw, L.nx - x0), kn = k1 - k0;
     const long long wx = L.nx, wy_ = (long long)L.ny * L.pitch, wz = (long long)L.nz * L.plane;
     if (bx == 0)
         for (int t = tid; t < jn * kn; t += nth) {
