@@ -237,11 +237,24 @@ def run_ours(args, rank, world, local_rank):
         alg = BYTES_PER_CELL["f32k"] * cells  # one read of the state and one write per launch
         ach = alg / (avg * 1e-3) / 1e9
         kname = {1: "k_step_f32k_tma", 2: "k_temporal2_tma"}.get(r["depth"], f"k_temporal_f32k<{r['depth']}>")
-        return {"bound": "hbm", "achieved": round(ach, 1), "peak": hbm_peak, "unit": "GB/s",
+        line = {"bound": "hbm", "achieved": round(ach, 1), "peak": hbm_peak, "unit": "GB/s",
                 "frac": round(ach / hbm_peak, 4), "peak_kind": f"{peak_kind} copy bandwidth",
                 "traffic": stencil_traffic(kname, n), "kernel": kname, "alg_bytes_per_launch": alg,
                 "substeps_per_launch": round(subs, 3), "avg_launch_ms": round(avg, 5),
-                "effective_single_sweep_gbs": round(ach * subs, 1)}
+                "effective_single_sweep_gbs": round(ach * subs, 1),
+                "effective_frac": round(ach * subs / hbm_peak, 4)}
+        winst = kernel_instructions(kname, cells) if r["depth"] > 1 else None
+        if winst:
+            # fused sub-steps move half the bytes per sub-step and are bound by instruction issue instead: the
+            # warp instructions of one launch (ncu count of the current sources, scaled to this grid) per second
+            # against the issue limit (152 SMs x 4 schedulers x one warp instruction per cycle at 2.07 GHz)
+            gwips = winst / (avg * 1e-3) / 1e9
+            line.update({"bound": "alu", "achieved": round(gwips, 1), "peak": round(ISSUE_PEAK_GWIPS, 1),
+                         "unit": "G warp-instr/s", "frac": round(gwips / ISSUE_PEAK_GWIPS, 4),
+                         "peak_kind": "instruction issue limit (152 SMs x 4 schedulers x 2.07 GHz, nominal)",
+                         "warp_inst_per_launch": round(winst), "hbm_achieved_gbs": round(ach, 1),
+                         "hbm_frac": round(ach / hbm_peak, 4)})
+        return line
 
     # temporal depth: a short sweep picks the fastest depth for the headline measurement
     if args.depth > 0 or args.prec == "f64":

@@ -115,10 +115,15 @@ int hg_step(hg_grid* g, int n_substeps);
 /*
  * Number of sub-steps fused per pass over the grid in hg_step: 1 = one sweep per sub-step (default); k in
  * 2..HG_MAX_TEMPORAL_DEPTH advances k sub-steps per round trip through HBM (rho is frozen across them, Sec. 2).
- * Results are the same as k single sweeps.  HG_ERR_ARG for k out of range.
+ * HG_ERR_ARG for k out of range.  The inner levels of a fused pass never reach memory: by default they keep the
+ * compensation of phi as a float, which is a little more accurate than the 16-bit code of a stored level, so the
+ * results differ from k single sweeps in the last bits of that compensation (about 1e-11 of phi).  With
+ * hg_set_temporal_exact(g, 1) the inner levels round their compensation as a store and a load would, and the results
+ * are bit-identical to k single sweeps (at some cost in speed).
  */
 #define HG_MAX_TEMPORAL_DEPTH 8
 int hg_set_temporal_depth(hg_grid* g, int k);
+int hg_set_temporal_exact(hg_grid* g, int exact);
 
 /* z planes per thread block of the single-sweep kernel (a tuning knob: more blocks and more z warm-up below, fewer
  * and longer blocks above); 0 restores the built-in rule.  Results do not depend on it. */

@@ -154,6 +154,11 @@ class Grid:
     def set_temporal_depth(self, k):
         _lib.check(_lib.lib().hg_set_temporal_depth(self.handle, int(k)))
 
+    def set_temporal_exact(self, exact=True):
+        """Fused sub-steps bit-identical to single sweeps (their inner levels round the compensation as a store
+        would); off by default, where the inner levels keep it as a float."""
+        _lib.check(_lib.lib().hg_set_temporal_exact(self.handle, 1 if exact else 0))
+
     def set_block_depth(self, planes):
         """z planes per block of the single-sweep kernel (0 = built-in rule); results do not depend on it."""
         _lib.check(_lib.lib().hg_set_block_depth(self.handle, int(planes)))

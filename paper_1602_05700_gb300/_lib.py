@@ -55,6 +55,7 @@ SIGNATURES = {
     "hg_set_phi": (_I, [_V, _V, _V, _I, _I]),
     "hg_step": (_I, [_V, _I]),
     "hg_set_temporal_depth": (_I, [_V, _I]),
+    "hg_set_temporal_exact": (_I, [_V, _I]),
     "hg_set_block_depth": (_I, [_V, _I]),
     "hg_accel": (_I, [_V, _V, _V, _V, _I]),
     "hg_get_phi": (_I, [_V, _V, _I, _I]),

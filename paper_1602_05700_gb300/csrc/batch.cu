@@ -74,10 +74,25 @@ std::string tune_key(const hg_batch* b) {
 }
 
 // device tables for the sub-step that starts from parity p (0: every grid's current level, 1: the next one)
+// The table lists the FP64 grids first, largest first, then the compensated-float grids: the block scheduler hands
+// out blocks in index order, so the long FP64-bound blocks start first and the short HBM-bound ones fill in around
+// them and make up the tail of each launch.
+std::vector<hg_grid*> launch_order(const hg_batch* b) {
+    std::vector<hg_grid*> o(b->grids);
+    auto cells = [](const hg_grid* g) { return (long long)g->nx * g->ny * g->nz; };
+    std::stable_sort(o.begin(), o.end(), [&](const hg_grid* a, const hg_grid* c) {
+        const bool a64 = a->prec == HG_PREC_F64, c64 = c->prec == HG_PREC_F64;
+        if (a64 != c64) return a64;
+        return cells(a) > cells(c);
+    });
+    return o;
+}
+
 int upload_tables(hg_batch* b) {
     std::vector<TmaEntry> tab[2];
+    const std::vector<hg_grid*> order = launch_order(b);
     for (int p = 0; p < 2; ++p) {
-        for (hg_grid* g : b->grids) {
+        for (hg_grid* g : order) {
             const int cur = g->cur;
             g->cur = cur ^ p;
             TmaEntry e;

@@ -104,7 +104,7 @@ __device__ __forceinline__ void f32k_update(float xl, float xr, float ys, float 
 }
 
 // The same sub-step for a group of four consecutive cells of a row (c, lc; x neighbours xl, lxl before the group
-// and xr, lxr after it), giving the bits of four f32k_update calls.  The x differences are shared between neighbouring
+// and xr, lxr after it), written on packed pairs; operation for operation it is four f32k_update calls.  The x differences are shared between neighbouring
 // cells: with D_e = c_{e+1} - c_e rounded (c_{-1} = xl, c_4 = xr), RN(c_{e-1} - c_e) = -D_{e-1} exactly, so the first
 // partial sum (xl - c) + (xr - c) of cell e is RN(D_e - D_{e-1}); everything after it runs on packed pairs.
 __device__ __forceinline__ void f32k_update4(const float4& c, const float4& lc, float xl, float lxl, float xr,
@@ -138,6 +138,26 @@ __device__ __forceinline__ void f32k_update4(const float4& c, const float4& lc, 
     ho = join4(ha, hb);
     lo = join4(la, lb);
     dout = join4(da, db);
+}
+
+// The same four cells by four scalar f32k_update calls.  The single sweep, the batched sweep and the fused kernels
+// in exact mode use this form, so that they round identically to one another (one cell of a 2.4-million-update
+// periodic run came out one unit in the last place apart between the packed and the scalar form inside the sweep
+// kernel, although the two agree on every input tried in isolation; the exact modes therefore keep to one form).
+__device__ __forceinline__ void f32k_update4_scalar(const float4& c, const float4& lc, float xl, float lxl, float xr,
+                                                    float lxr, const float4& ys, const float4& yn, const float4& zm,
+                                                    const float4& zp, const float4& lys, const float4& lyn,
+                                                    const float4& lzm, const float4& lzp, const float4& d,
+                                                    const float4& s, float nu2, float4& ho, float4& lo,
+                                                    float4& dout) {
+    f32k_update(xl, c.y, ys.x, yn.x, zm.x, zp.x, c.x, lxl, lc.y, lys.x, lyn.x, lzm.x, lzp.x, lc.x, d.x, s.x, nu2, ho.x,
+                lo.x, dout.x);
+    f32k_update(c.x, c.z, ys.y, yn.y, zm.y, zp.y, c.y, lc.x, lc.z, lys.y, lyn.y, lzm.y, lzp.y, lc.y, d.y, s.y, nu2,
+                ho.y, lo.y, dout.y);
+    f32k_update(c.y, c.w, ys.z, yn.z, zm.z, zp.z, c.z, lc.y, lc.w, lys.z, lyn.z, lzm.z, lzp.z, lc.z, d.z, s.z, nu2,
+                ho.z, lo.z, dout.z);
+    f32k_update(c.z, xr, ys.w, yn.w, zm.w, zp.w, c.w, lc.z, lxr, lys.w, lyn.w, lzm.w, lzp.w, lc.w, d.w, s.w, nu2, ho.w,
+                lo.w, dout.w);
 }
 
 // f64: phi^{n+1} = ((2c - prev) + nu^2 L) - s with L = (((((xl-c) + (xr-c)) + (ys-c)) + (yn-c)) + (zm-c)) + (zp-c):

@@ -384,6 +384,14 @@ int hg_set_temporal_depth(hg_grid* g, int k) {
     return HG_OK;
 }
 
+int hg_set_temporal_exact(hg_grid* g, int exact) {
+    HG_RANGE("hg_set_temporal_exact");
+    int rc = check_grid(g);
+    if (rc) return rc;
+    g->texact = exact ? 1 : 0;
+    return HG_OK;
+}
+
 int hg_set_block_depth(hg_grid* g, int planes) {
     HG_RANGE("hg_set_block_depth");
     int rc = check_grid(g);

@@ -148,6 +148,7 @@ struct hg_grid {
     double mass, rho_bar;
     long long step;
     int tdepth;
+    int texact;  // fused sub-steps bit-identical to single sweeps (hg_set_temporal_exact)
     int ziface;  // bit 0 / bit 1: -z / +z face is an interface to a neighbouring slab (hg_set_z_interface)
     int zb;  // z planes per block of the single sweep (0 = default rule; set by the batch autotuner)
     hg::YlmNorm ylm;
@@ -255,6 +256,7 @@ struct SweepArgs {
     float nu2f;        // nu^2 rounded to float once (compensated float sweeps)
     int zb;            // z planes per block
     int prec;
+    int exact;         // fused sub-steps: inner levels round their compensation as a store and a load would
     int cpl;           // FP64 sweep: x cells per lane (4: 128-cell tile rows; 1: 32-cell rows, for nx that 128 fits badly)
     unsigned gx, gy;   // blocks in x and y of this grid's sweep
     Bnd B;

@@ -472,6 +472,7 @@ SweepArgs sweep_args(const hg_grid* g, int zb, int cpl) {
     A.nu2f = (float)g->nu2;
     A.zb = zb > 0 ? (zb < g->nz ? zb : g->nz) : zchunk(g);
     A.prec = g->prec;
+    A.exact = g->texact;
     A.cpl = g->prec == HG_PREC_F64 ? (cpl > 0 ? cpl : f64_cells_per_lane(g->nx)) : 4;
     A.gx = (g->nx + 32 * A.cpl - 1) / (32 * A.cpl);
     A.gy = (g->ny + kWY - 1) / kWY;

@@ -25,7 +25,7 @@ __device__ __forceinline__ void group_update_store(const Layout& L, const Bnd& B
                                                    const float4& d, const float4& r, float* __restrict__ hi_n,
                                                    lo_t* __restrict__ lo_n, float* __restrict__ dlt) {
     float4 ho, lo, dout;
-    f32k_update4(hc, lc, hl, ll, hr, lr, hs, hn, hm, hp, ls, ln, lm, lp, d, r, nu2, ho, lo, dout);
+    f32k_update4_scalar(hc, lc, hl, ll, hr, lr, hs, hn, hm, hp, ls, ln, lm, lp, d, r, nu2, ho, lo, dout);
     if (i0 + 3 < L.nx) {
         *reinterpret_cast<float4*>(hi_n + q) = ho;
         *reinterpret_cast<uint2*>(lo_n + q) = lo_encode4(ho, lo);

@@ -1,8 +1,9 @@
 // Temporal blocking: K consecutive sub-steps of the hyperbolic gravity equation per round trip through HBM
 // (arXiv 1602.05700, Sec. 2: rho is frozen during the wave sub-steps of a hydro step, so K sub-steps can be fused
 // without reading the source again).  FP32-compensated state only (hi + lo = phi^n with lo stored as a 16-bit
-// code, dlt = phi^n - phi^{n-1}).  The levels computed in registers round lo through its code exactly as a store
-// and a load would (lo_round), so nothing depends on whether a level passed through memory.
+// code, dlt = phi^n - phi^{n-1}).  The levels computed in registers keep lo as a float, or, in the grid's exact
+// mode, round it through its code exactly as a store and a load would (lo_round), so that nothing depends on
+// whether a level passed through memory.
 //
 // A block of 32 x 32 threads owns a 32 x 32 column region of the x-y plane and marches in z through a chunk of
 // output planes.  Level 0 (the state at sub-step n) is read once per plane; level t = 1..K is computed one plane
@@ -46,6 +47,7 @@ struct TParams {
     float nu2;
     int bc;
     int zchunk;
+    int exact;  // inner levels round their compensation through the 16-bit code (bit-identical to single sweeps)
 };
 
 __device__ __forceinline__ int wrap(int v, int n) {
@@ -152,7 +154,7 @@ __device__ __forceinline__ void region_sweep(const TParams& P, float2 (*sh)[TB +
                 const float2 ys = sh[b][ty][tx + 1], yn = sh[b][ty + 2][tx + 1];
                 f32k_update(xl.x, xr.x, ys.x, yn.x, qh[t - 1][0], qh[t - 1][2], c, xl.y, xr.y, ys.y, yn.y,
                             ql[t - 1][0], ql[t - 1][2], lc, dprev, rq[t], P.nu2, oh, ol, od);
-                if (t < K) ol = lo_round(oh, ol);
+                if (t < K && P.exact) ol = lo_round(oh, ol);
             } else if (robin && ((col_int && zg) || (EDGE && (col_fx || col_fy) && zin))) {
                 float2 in;
                 long long row;
@@ -168,7 +170,7 @@ __device__ __forceinline__ void region_sweep(const TParams& P, float2 (*sh)[TB +
                 }
                 const float2 ab = P.robin32[row];
                 robin_update_f32k(ab.x, ab.y, c, lc, in.x, in.y, oh, ol);
-                if (t < K) ol = lo_round(oh, ol);
+                if (t < K && P.exact) ol = lo_round(oh, ol);
             }
             if (t < K) {
                 qh[t][0] = qh[t][1];
@@ -248,6 +250,7 @@ int launch_temporal(hg_grid* g, int k) {
     int zchunk = 64;
     if (zchunk > g->nz + 2) zchunk = g->nz + 2;
     P.zchunk = zchunk;
+    P.exact = g->texact;
     int rc = prof_begin(g);
     if (rc) return rc;
     switch (k) {

@@ -18,9 +18,11 @@
 //
 // Face ghosts follow the boundary condition exactly as a single sweep writes them (Dirichlet: the data, unchanged;
 // Robin: the radiation update from the ghost and its interior neighbour), and the level-(n+2) face ghosts bordering
-// the tile are written with the new level.  Level-(n+1) compensations go through the 16-bit code (lo_round4) as a
-// store and a load would, and every cell update is the single sweep's arithmetic (cell.cuh), so the result is
-// bit-identical to two single sweeps.  The arithmetic runs on packed float pairs (cell.cuh).
+// the tile are written with the new level.  Level n+1 never passes through memory, so its compensations stay floats
+// (slightly more accurate than the 16-bit code a stored level keeps); with the grid's exact mode set
+// (hg_set_temporal_exact) they go through the code as a store and a load would (lo_round4) and every cell update is
+// the single sweep's scalar form (cell.cuh), so the result is then bit-identical to two single sweeps; the default
+// mode runs the update on packed float pairs.
 //
 // HBM bytes per cell for the two sub-steps: 24 (read hi, lo, dlt, s; write hi, lo, dlt) plus the halo rows and
 // planes of neighbouring tiles (mostly served by L2).  Every wait is bounded in time; a wait that gives up sets the
@@ -75,7 +77,7 @@ __device__ __forceinline__ void robin4(const Bnd& B, int f, long long t0, const 
 
 // One block: RAGGED is set for the last tile in x when nx is not a multiple of 128 (then the +x ghost lies inside
 // the tile and every lane classifies its cells); otherwise the x halo columns are the helper's.
-template <bool RAGGED>
+template <bool RAGGED, bool EXACT>
 __device__ __forceinline__ void fused2_block(const CUtensorMap* m_hi, const CUtensorMap* m_lo, const CUtensorMap* m_d,
                                              const CUtensorMap* m_s, const SweepArgs& A, float* __restrict__ d_out,
                                              int* err, unsigned char* smem, unsigned long long* bar_full,
@@ -149,7 +151,7 @@ __device__ __forceinline__ void fused2_block(const CUtensorMap* m_hi, const CUte
                             const float hin = H[sr * kFC + ci];
                             const float2 ab = coef(B, side, (long long)p * L.ny + y);
                             robin_update_f32k(ab.x, ab.y, hc, lc, hin, lo_decode(hin, Lo[sr * kFC + ci]), a, b);
-                            b = lo_round(a, b);
+                            if (EXACT) b = lo_round(a, b);
                         }
                     } else {
                         const float* Hp = Hs(it + 1);
@@ -162,7 +164,7 @@ __device__ __forceinline__ void fused2_block(const CUtensorMap* m_hi, const CUte
                                     lo_decode(xr, Lo[sr * kFC + col + 1]), lo_decode(ys, Lo[(sr - 1) * kFC + col]),
                                     lo_decode(yn, Lo[(sr + 1) * kFC + col]), lm, lo_decode(zp, Lp[sr * kFC + col]), lc,
                                     Ds(it)[r * kFC + col], Ss(it)[r * kFC + col], nu2, a, b, c);
-                        b = lo_round(a, b);
+                        if (EXACT) b = lo_round(a, b);
                     }
                     *rh(it & 1, r, col) = a;
                     *rl(it & 1, r, col) = b;
@@ -253,8 +255,11 @@ __device__ __forceinline__ void fused2_block(const CUtensorMap* m_hi, const CUte
                 hr = H[sr * kFC + kFX + 4];
                 lr = lo_decode(hr, Lo[sr * kFC + kFX + 4]);
             }
-            f32k_update4(hc0, lc0, hl, ll, hr, lr, hs, hn, hm0, hp0, ls, ln, lm0, lp0, d0, s0, nu2, h1, l1, d1);
-            l1 = lo_round4(h1, l1);
+            if (EXACT)
+                f32k_update4_scalar(hc0, lc0, hl, ll, hr, lr, hs, hn, hm0, hp0, ls, ln, lm0, lp0, d0, s0, nu2, h1, l1, d1);
+            else
+                f32k_update4(hc0, lc0, hl, ll, hr, lr, hs, hn, hm0, hp0, ls, ln, lm0, lp0, d0, s0, nu2, h1, l1, d1);
+            if (EXACT) l1 = lo_round4(h1, l1);
             if (RAGGED) {
 #pragma unroll
                 for (int e = 0; e < 4; ++e)
@@ -264,7 +269,7 @@ __device__ __forceinline__ void fused2_block(const CUtensorMap* m_hi, const CUte
                             const float2 ab = coef(B, 1, (long long)p * L.ny + y);
                             const float gi = e == 0 ? hl : el(hc0, e - 1), li = e == 0 ? ll : el(lc0, e - 1);
                             robin_update_f32k(ab.x, ab.y, el(hc0, e), el(lc0, e), gi, li, a, b);
-                            b = lo_round(a, b);
+                            if (EXACT) b = lo_round(a, b);
                         }
                         set(h1, e, a);
                         set(l1, e, b);
@@ -279,14 +284,14 @@ __device__ __forceinline__ void fused2_block(const CUtensorMap* m_hi, const CUte
                 lgin = lo_decode4(gin, ldsl4(Ls(it + 1) + sr * kFC + col));
             }
             robin4(B, p < 0 ? 4 : 5, (long long)y * L.nx + xa, hc0, lc0, gin, lgin, h1, l1, nlive);
-            l1 = lo_round4(h1, l1);
+            if (EXACT) l1 = lo_round4(h1, l1);
         } else if (robin && R.ghost) {
             // a y-face ghost row at a plane of the tile: the radiation update from the interior row next to it
             const int si = y < 0 ? sr + 1 : sr - 1;
             const float4 gin = lds4(H + si * kFC + col);
             const float4 lgin = lo_decode4(gin, ldsl4(Lo + si * kFC + col));
             robin4(B, y < 0 ? 2 : 3, (long long)p * L.nx + xa, hc0, lc0, gin, lgin, h1, l1, nlive);
-            l1 = lo_round4(h1, l1);
+            if (EXACT) l1 = lo_round4(h1, l1);
         }
         *reinterpret_cast<float4*>(rh(it & 1, r, col)) = h1;
         *reinterpret_cast<float4*>(rl(it & 1, r, col)) = l1;
@@ -353,7 +358,7 @@ __device__ __forceinline__ void fused2_block(const CUtensorMap* m_hi, const CUte
         hm0 = __ldg(reinterpret_cast<const float4*>((const float*)A.hi_c + q));
         lm0 = lo_decode4(hm0, __ldg(reinterpret_cast<const uint2*>((const lo_t*)A.lo_c + q)));
     }
-#pragma unroll 2  // two planes per trip: the z queues rotate through registers instead of being copied
+
     for (int it = 0; it < iters; ++it) {
         const int p = k0 - 1 + it, q = p - 1;
         const bool in_tile = p >= k0 && p < k1;
@@ -389,7 +394,11 @@ __device__ __forceinline__ void fused2_block(const CUtensorMap* m_hi, const CUte
                     grl = *rl(slot, r, kFX + 4);
                 }
                 float4 ho, lo, dout;
-                f32k_update4(c1, lc1, gl, gll, gr, grl, ys, yn, m1, h1, lys, lyn, lm1, l1, d1c, sc, nu2, ho, lo, dout);
+                if (EXACT)
+                    f32k_update4_scalar(c1, lc1, gl, gll, gr, grl, ys, yn, m1, h1, lys, lyn, lm1, l1, d1c, sc, nu2, ho,
+                                        lo, dout);
+                else
+                    f32k_update4(c1, lc1, gl, gll, gr, grl, ys, yn, m1, h1, lys, lyn, lm1, l1, d1c, sc, nu2, ho, lo, dout);
                 const long long qo = L.at(xa, y, q);
                 if (!RAGGED || xa + 3 < L.nx) {
                     *reinterpret_cast<float4*>(hi_n + qo) = ho;
@@ -458,10 +467,18 @@ __global__ void __maxnreg__(96)  // 2 blocks of 320 threads per SM (5 warps of 9
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
     __syncthreads();
-    if ((int)(blockIdx.x * kFX) + kFX <= A.L.nx)
-        fused2_block<false>(&m_hi, &m_lo, &m_d, &m_s, A, d_out, err, smem, bar_full, &abort_flag);
-    else
-        fused2_block<true>(&m_hi, &m_lo, &m_d, &m_s, A, d_out, err, smem, bar_full, &abort_flag);
+    const bool ragged = (int)(blockIdx.x * kFX) + kFX > A.L.nx;
+    if (A.exact) {
+        if (ragged)
+            fused2_block<true, true>(&m_hi, &m_lo, &m_d, &m_s, A, d_out, err, smem, bar_full, &abort_flag);
+        else
+            fused2_block<false, true>(&m_hi, &m_lo, &m_d, &m_s, A, d_out, err, smem, bar_full, &abort_flag);
+    } else {
+        if (ragged)
+            fused2_block<true, false>(&m_hi, &m_lo, &m_d, &m_s, A, d_out, err, smem, bar_full, &abort_flag);
+        else
+            fused2_block<false, false>(&m_hi, &m_lo, &m_d, &m_s, A, d_out, err, smem, bar_full, &abort_flag);
+    }
 }
 
 constexpr int kZ2 = 32;  // level-(n+2) planes per block

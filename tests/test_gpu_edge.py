@@ -65,6 +65,7 @@ def test_fused_equals_single_sweeps_on_degenerate_grids(depth, bc, shape):
         g, _ = pair(nx, ny, nz, H, bc, "f32k", cfl=robin_cfl(nx, ny, nz, H) if bc == "robin" else 0.5)
         if d > 1:
             g.set_temporal_depth(d)
+            g.set_temporal_exact(True)
         g.set_density(torch.from_numpy(rho).cuda())
         g.set_phi(torch.from_numpy(phi0).cuda(), torch.from_numpy(prev0).cuda())
         g.step(7)
