@@ -511,7 +511,46 @@ def run_batch(args):
     res["sequential_per_grid"] = {"ms": round(ms_s, 2), "gcell_updates_per_s": round(cells * T / (ms_s * 1e-3) / 1e9, 2)}
     res["speedup"] = round(ms_s / ms_b, 3)
     f32 = [i for i in range(48) if i % 2 == 0]
-    res["f32k_cells"] = int(sum(int(sides[i]) ** 3 for i in f32))
+    f32_cells = int(sum(int(sides[i]) ** 3 for i in f32))
+    f64_cells = cells - f32_cells
+    res["f32k_cells"] = f32_cells
+    for g in gs + gs2:
+        g.free()
+    b.free()
+
+    # each precision alone in a batch of its own grids, and the floor of the mixed batch: the FP64 grids at the FP64
+    # rate of a large grid (512^3, 128-cell tile rows, the pipe-bound rate) and the float grids at theirs
+    def batch_alone(idx):
+        gsub = []
+        for i, g in enumerate(grids()):
+            if i in idx:
+                gsub.append(g)
+            else:
+                g.free()
+        bb = hg.Batch(gsub)
+        bb.step(8)
+        torch.cuda.synchronize()
+        e0.record()
+        bb.step(T)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        info = bb.info()
+        bb.free()
+        for g in gsub:
+            g.free()
+        return ms, info
+
+    ms32, info32 = batch_alone(set(f32))
+    ms64, info64 = batch_alone(set(range(48)) - set(f32))
+    hbm_peak, _ = peaks()
+    res["f32k_only_batch"] = {"ms": round(ms32, 2), "gcell_updates_per_s": round(f32_cells * T / (ms32 * 1e-3) / 1e9, 2),
+                              "single_sweep_roofline_gcells": round(hbm_peak / BYTES_PER_CELL["f32k"], 1), **info32}
+    res["f64_only_batch"] = {"ms": round(ms64, 2), "gcell_updates_per_s": round(f64_cells * T / (ms64 * 1e-3) / 1e9, 2),
+                             **info64}
+    res["mixed_floor_ms"] = {"f64_alone_plus_f32k_alone": round(ms64 + ms32, 2), "f64_alone": round(ms64, 2),
+                             "note": "overlapping the HBM-bound float blocks with the FP64-bound ones can hide the "
+                                     "float part; the FP64 part alone is the floor"}
     return res
 
 
