@@ -23,6 +23,9 @@
  *     No call aborts, traps or waits without bound: every wait inside a kernel has a time limit (1 s), after which
  *     the kernel records the failure in the grid's device error word and returns; hg_sync and hg_get_stats then
  *     report HG_ERR_TIMEOUT.
+ *   - Debug builds (the library compiled with -DHG_DEBUG) also check, before every global store of the sub-step
+ *     kernels, that the padded index range lies inside its array; a range outside is not stored and sets a second
+ *     bit of the error word, which hg_sync and hg_get_stats report as HG_ERR_BOUNDS.  Release builds carry no checks.
  *   - Array arguments are plain pointers.  Unless stated otherwise an array is nz*ny*nx elements in C order
  *     (z slowest, x fastest), no padding, of the element type given by a dtype argument (HG_DT_F32 = float,
  *     HG_DT_F64 = double).  A flag *_on_device says whether a pointer is device memory of the grid's device
@@ -48,6 +51,7 @@ extern "C" {
 #define HG_ERR_NONFINITE (-4) /* a NaN or Inf was found in the state (hg_get_stats) */
 #define HG_ERR_TIMEOUT (-5)   /* a bounded device-side wait gave up */
 #define HG_ERR_STATE (-6)     /* call not valid in the grid's current state */
+#define HG_ERR_BOUNDS (-7)    /* debug builds: a sub-step kernel computed a store index outside its array */
 
 /* storage / arithmetic precision of a grid's state */
 #define HG_PREC_F32K 0 /* float storage, compensated (Kahan-style) increments of phi */
@@ -233,6 +237,16 @@ int hg_io_wait(hg_grid* g, int keep);
  * error of an earlier launch if one was pending.  Synchronises the stream.
  */
 int hg_check_bounded_wait(hg_grid* g);
+
+/*
+ * Diagnostic of the debug build's index checks: launches a one-thread kernel that passes the index one past the
+ * grid's padded array (never stored) to the same check the sub-step kernels use, then reads the error word as hg_sync
+ * does.  Returns HG_OK when the check fired and HG_ERR_BOUNDS was reported (the error word is cleared again),
+ * HG_ERR_STATE when it was not, the error of an earlier launch if one was pending, and HG_ERR_STATE without launching
+ * anything in a release build.  hg_is_debug_build() tells which build is loaded (1 debug, 0 release).
+ */
+int hg_check_bounds(hg_grid* g);
+int hg_is_debug_build(void);
 
 /* Block until the grid's streams are idle; HG_ERR_CUDA carries any pending asynchronous error. */
 int hg_sync(hg_grid* g);

@@ -31,12 +31,18 @@ BC = {"dirichlet": HG_BC_DIRICHLET_ANALYTIC, "dirichlet_analytic": HG_BC_DIRICHL
       "robin": HG_BC_ROBIN, "periodic": HG_BC_PERIODIC}
 PREC = {"f32k": HG_PREC_F32K, "f64": HG_PREC_F64}
 
-__all__ = ["Grid", "Batch", "Hydro", "HGError", "BC", "PREC", "build"]
+__all__ = ["Grid", "Batch", "Hydro", "HGError", "BC", "PREC", "build", "is_debug_build"]
 
 
-def build(force: bool = False) -> str:
+def build(force: bool = False, debug: bool = False) -> str:
+    """Build the CUDA library in-tree (debug=True: the HG_DEBUG variant with index checks)."""
     from .builder import build as _b
-    return _b(force=force)
+    return _b(force=force, debug=debug)
+
+
+def is_debug_build() -> bool:
+    """Whether the loaded library is the HG_DEBUG variant (HG_DEBUG=1 in the environment at import)."""
+    return bool(_lib.lib().hg_is_debug_build())
 
 
 def probe_rate(kind: str) -> dict:
@@ -210,6 +216,11 @@ class Grid:
     def check_bounded_wait(self):
         """Run the kernels' bounded-wait diagnostic (a wait that cannot complete must give up and be reported)."""
         _lib.check(_lib.lib().hg_check_bounded_wait(self.handle))
+
+    def check_bounds(self):
+        """Debug builds: run the index-check diagnostic (an index past the array must be caught and reported as
+        HG_ERR_BOUNDS, with nothing stored).  A release build raises HGError(HG_ERR_STATE)."""
+        _lib.check(_lib.lib().hg_check_bounds(self.handle))
 
     def io_wait(self, keep=0):
         """Block until all but the newest `keep` io_step calls are done (their outputs are then filled)."""

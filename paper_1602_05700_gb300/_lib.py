@@ -1,7 +1,8 @@
 """ctypes declarations of the C ABI in include/hg.h and include/hg_hydro.h (argument marshalling only).
 
-The library is loaded from paper_1602_05700_gb300/_build/libhypergrav.so.  There is no other implementation:
-if the library is missing, every call raises.
+The library is loaded from paper_1602_05700_gb300/_build/libhypergrav.so, or from its checked variant
+_build/libhypergrav_debug.so when the environment sets HG_DEBUG=1 (the same ABI, with index checks before the
+sub-step kernels' stores).  There is no other implementation: if the library is missing, every call raises.
 """
 from __future__ import annotations
 
@@ -9,7 +10,8 @@ import ctypes
 import os
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "_build", "libhypergrav.so")
+DEBUG = os.environ.get("HG_DEBUG", "0") not in ("", "0")
+LIB_PATH = os.path.join(HERE, "_build", "libhypergrav_debug.so" if DEBUG else "libhypergrav.so")
 
 HG_OK = 0
 HG_ERR_ARG = -1
@@ -18,6 +20,7 @@ HG_ERR_CUDA = -3
 HG_ERR_NONFINITE = -4
 HG_ERR_TIMEOUT = -5
 HG_ERR_STATE = -6
+HG_ERR_BOUNDS = -7
 
 HG_PREC_F32K = 0
 HG_PREC_F64 = 1
@@ -104,6 +107,8 @@ SIGNATURES = {
     "hg_hydro_profile": (_I, [_V, _I]),
     "hg_hydro_profile_read": (_I, [_V, _P(_D), _P(ctypes.c_longlong)]),
     "hg_hydro_free": (None, [_V]),
+    "hg_check_bounds": (_I, [_V]),
+    "hg_is_debug_build": (_I, []),
 }
 
 _lib = None
@@ -115,7 +120,7 @@ def lib():
     if _lib is None:
         if not os.path.exists(LIB_PATH):
             raise RuntimeError(f"CUDA library {LIB_PATH} is missing: run paper_1602_05700_gb300.build() "
-                               "(or __graft_entry__.build()) first")
+                               "(debug=True for the HG_DEBUG variant, or __graft_entry__.build()) first")
         L = ctypes.CDLL(LIB_PATH)
         for name, (res, args) in SIGNATURES.items():
             fn = getattr(L, name)

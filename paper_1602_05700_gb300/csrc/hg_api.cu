@@ -140,8 +140,11 @@ int device_error(hg_grid* g) {
     HG_CUDA(cudaStreamSynchronize(g->stream));
     if (!e) return HG_OK;
     HG_CUDA(cudaMemsetAsync(g->derr, 0, sizeof e, g->stream));
-    return fail(HG_ERR_TIMEOUT, "a bounded wait inside a sub-step kernel gave up (the results of that launch are "
-                                "not valid)");
+    if (e & 1)
+        return fail(HG_ERR_TIMEOUT, "a bounded wait inside a sub-step kernel gave up (the results of that launch are "
+                                    "not valid)");
+    return fail(HG_ERR_BOUNDS, "a sub-step kernel computed a store index outside its array (debug build; the store "
+                               "was skipped, the results are not valid)");
 }
 
 int prof_fold(hg_grid* g) {
@@ -915,6 +918,21 @@ int hg_check_bounded_wait(hg_grid* g) {
     rc = wait_selftest(g);
     if (rc == HG_ERR_TIMEOUT) return HG_OK;  // the wait gave up and the host saw it
     if (rc == HG_OK) return fail(HG_ERR_STATE, "the bounded-wait self-test did not report its timeout");
+    return rc;
+}
+
+int hg_is_debug_build(void) { return kDebugChecks ? 1 : 0; }
+
+int hg_check_bounds(hg_grid* g) {
+    HG_RANGE("hg_check_bounds");
+    int rc = check_grid(g);
+    if (rc) return rc;
+    if (!kDebugChecks) return fail(HG_ERR_STATE, "a release build has no index checks");
+    if ((rc = device_error(g))) return rc;
+    if ((rc = bounds_selftest(g))) return rc;
+    rc = device_error(g);
+    if (rc == HG_ERR_BOUNDS) return HG_OK;
+    if (rc == HG_OK) return fail(HG_ERR_STATE, "the index check did not report the index past the array");
     return rc;
 }
 

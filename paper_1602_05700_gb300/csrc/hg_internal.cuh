@@ -23,6 +23,25 @@ struct NvtxRange {
 };
 #define HG_RANGE(name) ::hg::NvtxRange hg_nvtx_range_(name)
 
+// Debug builds (-DHG_DEBUG; builder.build(debug=True) makes _build/libhypergrav_debug.so, loaded when the environment
+// sets HG_DEBUG=1): before each global store of the sub-step kernels the padded index range is checked against the
+// array; a range outside sets bit value 2 of the grid's error word (reported as HG_ERR_BOUNDS) and the store is
+// skipped -- no trap, no fault.  Release builds compile the check to `true`.
+#ifdef HG_DEBUG
+constexpr bool kDebugChecks = true;
+#else
+constexpr bool kDebugChecks = false;
+#endif
+__device__ __forceinline__ bool idx_ok(long long q, int n, long long size, int* err) {
+    if constexpr (kDebugChecks) {
+        if (q < 0 || q + n > size) {
+            if (err) atomicOr(err, 2);
+            return false;
+        }
+    }
+    return true;
+}
+
 
 // ---- device memory layout ------------------------------------------------------------------------------------
 // Every per-cell field of a grid lives in one "padded" array of pitch * (ny+2) * (nz+2) elements: z-planes of
@@ -140,7 +159,8 @@ struct hg_grid {
     long long red_elems;
     double* dres;   // small device result buffer
     double* dsum;   // sum(rho) of the last density, written on the device by the source preparation
-    int* derr;      // device error word: a bounded wait in a kernel gave up (reported as HG_ERR_TIMEOUT)
+    int* derr;      // device error word: value 1 a bounded wait in a kernel gave up (HG_ERR_TIMEOUT), value 2 a debug
+                    // index check failed (HG_ERR_BOUNDS)
     int mass_pending;  // mass / rho_bar below not yet read back from dsum
     double* staging;  // dense nz*ny*nx doubles, allocated on first host transfer
     double Q[hg::kMaxQ];
@@ -212,6 +232,7 @@ int device_error(hg_grid* g);                        // HG_ERR_TIMEOUT if a kern
 // raise a kernel's dynamic shared-memory limit once per device (the attribute is per device); `done` holds one bit
 // per device id
 int smem_attr_once(const void* fn, int bytes, unsigned long long* done);
+int bounds_selftest(hg_grid* g);                     // the debug index check on an index past the array (stencil_tma.cu)
 int wait_selftest(hg_grid* g);                       // a wait that cannot complete, then device_error (stencil_tma.cu)
 int ensure_staging(hg_grid* g);
 int prepare_source(hg_grid* g, const void* src, int dtype);  // dense rho -> stored s, sum(rho) -> dsum (no sync)
@@ -241,6 +262,7 @@ struct Bnd {
     const float2* robin32;  // (alpha, beta) per face ghost, compensated float grids
     const double* robin;    // (a = nu/mu, r_g, r_i) per face ghost, FP64 grids
     long long off[7];       // face offsets in the ghost enumeration (hg::Faces)
+    int* err;               // the grid's device error word (debug index checks)
 };
 
 // Everything one sweep of one grid needs (a launch of one grid, or one entry of a batched launch).

@@ -285,7 +285,8 @@ __device__ __forceinline__ void sweep_f64(const SweepArgs& A, int bx, int by, in
                 double rr = e == C - 1 ? xr : cc.v[e + 1];
                 o.v[e] = f64_update(l, rr, ys.v[e], yn.v[e], cm.v[e], cp.v[e], cc.v[e], pv.v[e], r.v[e], nu2);
             }
-            if (C == 4 && full) {
+            if (!idx_ok(q, C, L.elems, B.err)) {
+            } else if (C == 4 && full) {
                 st2(phi_pn + q, make_double2(o.v[0], o.v[1]));
                 st2(phi_pn + q + 2, make_double2(o.v[C > 2 ? 2 : 0], o.v[C > 3 ? 3 : 0]));
             } else {
@@ -312,12 +313,15 @@ __device__ __forceinline__ void sweep_f64(const SweepArgs& A, int bx, int by, in
                 }
 #pragma unroll
             for (int u = 0; u < kGB; ++u)
-                if (u < gb.n) phi_pn[gb.qg[u]] = robin_update_f64(a[u], rg[u], ri[u], pg[u], pi[u]);
+                if (u < gb.n && idx_ok(gb.qg[u], 1, L.elems, B.err))
+                    phi_pn[gb.qg[u]] = robin_update_f64(a[u], rg[u], ri[u], pg[u], pi[u]);
         }, TW);
     if (B.periodic) {
         __syncthreads();
         block_periodic_copies(L, bx * TW, by * WY, WY, k0, k1, bx, by, A.gx, A.gy, block_tid(), block_nth(),
-                              [&](long long q, long long d) { phi_pn[d] = phi_pn[q]; }, TW);
+                              [&](long long q, long long d) {
+                                  if (idx_ok(d, 1, L.elems, B.err)) phi_pn[d] = phi_pn[q];
+                              }, TW);
     }
 }
 
@@ -373,11 +377,13 @@ __global__ void __launch_bounds__(256) k_ghosts_robin(const SweepArgs A, int t0)
         const float hg = __ldg(hc + qg), hi = __ldg(hc + qi);
         float gh, gl;
         robin_update_f32k(ab.x, ab.y, hg, lo_decode(hg, lc[qg]), hi, lo_decode(hi, lc[qi]), gh, gl);
+        if (!idx_ok(qg, 1, A.L.elems, A.B.err)) return;
         ((float*)A.hi_n)[qg] = gh;
         ((lo_t*)A.lo_n)[qg] = lo_encode(gh, gl);
     } else {
         const double* pc = (const double*)A.hi_c;
         const double* R = A.B.robin;
+        if (!idx_ok(qg, 1, A.L.elems, A.B.err)) return;
         ((double*)A.hi_n)[qg] = robin_update_f64(R[3 * t], R[3 * t + 1], R[3 * t + 2], __ldg(pc + qg), __ldg(pc + qi));
     }
 }
@@ -480,6 +486,7 @@ SweepArgs sweep_args(const hg_grid* g, int zb, int cpl) {
     A.B.periodic = g->bc == HG_BC_PERIODIC ? 1 : 0;
     A.B.xfaces = 0;
     A.B.zskip = g->ziface;
+    A.B.err = g->derr;
     A.B.robin32 = g->robin32;
     A.B.robin = g->robin;
     for (int f = 0; f < 7; ++f) A.B.off[f] = g->F.off[f];

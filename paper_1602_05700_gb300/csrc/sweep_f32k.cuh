@@ -26,6 +26,7 @@ __device__ __forceinline__ void group_update_store(const Layout& L, const Bnd& B
                                                    lo_t* __restrict__ lo_n, float* __restrict__ dlt) {
     float4 ho, lo, dout;
     f32k_update4_scalar(hc, lc, hl, ll, hr, lr, hs, hn, hm, hp, ls, ln, lm, lp, d, r, nu2, ho, lo, dout);
+    if (!idx_ok(q, 4, L.elems, B.err)) return;
     if (i0 + 3 < L.nx) {
         *reinterpret_cast<float4*>(hi_n + q) = ho;
         *reinterpret_cast<uint2*>(lo_n + q) = lo_encode4(ho, lo);
@@ -43,11 +44,11 @@ __device__ __forceinline__ void group_update_store(const Layout& L, const Bnd& B
     // hold the face cells: the ghosts lie in the same rows, so these are the only scattered stores
     if (B.xfaces == HG_BC_PERIODIC) {
         const int elast = L.nx - 1 - i0;  // element holding cell nx-1, if 0..3
-        if (i0 == 0) {
+        if (i0 == 0 && idx_ok(q + L.nx, 1, L.elems, B.err)) {
             hi_n[q + L.nx] = ho.x;
             lo_n[q + L.nx] = lo_encode(ho.x, lo.x);
         }
-        if (elast >= 0 && elast < 4) {
+        if (elast >= 0 && elast < 4 && idx_ok(q + elast - L.nx, 1, L.elems, B.err)) {
             hi_n[q + elast - L.nx] = el(ho, elast);
             lo_n[q + elast - L.nx] = lo_encode(el(ho, elast), el(lo, elast));
         }

@@ -211,8 +211,10 @@ __device__ __forceinline__ void tma_sweep(const CUtensorMap* m_hi, const CUtenso
                     robin_update_f32k(ax.x, ax.y, hg, lo_decode(hg, Lo[row + tg]), hin, lo_decode(hin, Lo[row + ti]),
                                       gh, gl);
                     const long long q = L.at(side ? L.nx : -1, jx, k);
-                    hi_n[q] = gh;
-                    lo_n[q] = lo_encode(gh, gl);
+                    if (idx_ok(q, 1, L.elems, B.err)) {
+                        hi_n[q] = gh;
+                        lo_n[q] = lo_encode(gh, gl);
+                    }
                 }
 #pragma unroll
                 for (int s2 = 0; s2 < 2; ++s2) {
@@ -228,8 +230,10 @@ __device__ __forceinline__ void tma_sweep(const CUtensorMap* m_hi, const CUtenso
                             robin_update_f32k(ay[s2][e].x, ay[s2][e].y, hg, lo_decode(hg, Lo[rg * kHX + t]), hin,
                                               lo_decode(hin, Lo[ri * kHX + t]), gh, gl);
                             const long long q = L.at(i, s2 ? L.ny : -1, k);
-                            hi_n[q] = gh;
-                            lo_n[q] = lo_encode(gh, gl);
+                            if (idx_ok(q, 1, L.elems, B.err)) {
+                                hi_n[q] = gh;
+                                lo_n[q] = lo_encode(gh, gl);
+                            }
                         }
                     }
                 }
@@ -278,6 +282,7 @@ __device__ __forceinline__ void tma_sweep(const CUtensorMap* m_hi, const CUtenso
                 const float2 ab = B.robin32[B.off[f] + (long long)j * L.nx + i0 + e];
                 float gh, gl;
                 robin_update_f32k(ab.x, ab.y, el(hg, e), el(lg, e), el(hin, e), el(lin, e), gh, gl);
+                if (!idx_ok(qg + e, 1, L.elems, B.err)) continue;
                 hi_n[qg + e] = gh;
                 lo_n[qg + e] = lo_encode(gh, gl);
             }
@@ -325,6 +330,7 @@ __device__ __forceinline__ void tma_sweep(const CUtensorMap* m_hi, const CUtenso
         if (ok)
             block_periodic_copies(L, x0, j0, WY, k0, k1, bx, by, A.gx, A.gy, tid, 32 * WY,
                                   [&](long long qs, long long qd) {
+                                      if (!idx_ok(qd, 1, L.elems, B.err)) return;
                                       hi_n[qd] = hi_n[qs];
                                       lo_n[qd] = lo_n[qs];
                                   });

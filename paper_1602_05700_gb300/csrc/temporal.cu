@@ -48,6 +48,7 @@ struct TParams {
     int bc;
     int zchunk;
     int exact;  // inner levels round their compensation through the 16-bit code (bit-identical to single sweeps)
+    int* err;   // the grid's device error word (debug index checks)
 };
 
 __device__ __forceinline__ int wrap(int v, int n) {
@@ -183,7 +184,8 @@ __device__ __forceinline__ void region_sweep(const TParams& P, float2 (*sh)[TB +
                 dq[t][1] = od;
             } else if (out_col && pt >= z0 && pt < z1) {
                 const long long q = L.at(x, y, pt);
-                if (periodic) {
+                if (!idx_ok(q, 1, L.elems, P.err)) {
+                } else if (periodic) {
                     // interior cells, and the face ghosts as copies of the wrapped cells (the same values the
                     // blocks owning those cells compute, from the same inputs)
                     const int nout = (x < 0 || x >= L.nx) + (y < 0 || y >= L.ny) + (pt < 0 || pt >= L.nz);
@@ -251,6 +253,7 @@ int launch_temporal(hg_grid* g, int k) {
     if (zchunk > g->nz + 2) zchunk = g->nz + 2;
     P.zchunk = zchunk;
     P.exact = g->texact;
+    P.err = g->derr;
     int rc = prof_begin(g);
     if (rc) return rc;
     switch (k) {

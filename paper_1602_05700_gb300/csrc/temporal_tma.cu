@@ -181,8 +181,10 @@ __device__ __forceinline__ void fused2_block(const CUtensorMap* m_hi, const CUte
                 robin_update_f32k(ab.x, ab.y, *rh(slot, r, col), *rl(slot, r, col), *rh(slot, r, ci),
                                   *rl(slot, r, ci), a, b);
                 const long long qi = L.at(xh, y, q);
-                hi_n[qi] = a;
-                lo_n[qi] = lo_encode(a, b);
+                if (idx_ok(qi, 1, L.elems, B.err)) {
+                    hi_n[qi] = a;
+                    lo_n[qi] = lo_encode(a, b);
+                }
             }
             __syncthreads();
             if (lane == 0 && !*abort_flag && it + kFS < nload) {  // every warp is done with plane p's stage
@@ -308,6 +310,7 @@ __device__ __forceinline__ void fused2_block(const CUtensorMap* m_hi, const CUte
         float4 ho, lo;
         robin4(B, R.y < 0 ? 2 : 3, (long long)q * L.nx + xa, hg, lg, gin, lgin, ho, lo, nlive);
         const long long qo = L.at(xa, R.y, q);
+        if (!idx_ok(qo, nlive, L.elems, B.err)) return;
 #pragma unroll
         for (int e = 0; e < 4; ++e)
             if (e < nlive) {
@@ -400,7 +403,8 @@ __device__ __forceinline__ void fused2_block(const CUtensorMap* m_hi, const CUte
                 else
                     f32k_update4(c1, lc1, gl, gll, gr, grl, ys, yn, m1, h1, lys, lyn, lm1, l1, d1c, sc, nu2, ho, lo, dout);
                 const long long qo = L.at(xa, y, q);
-                if (!RAGGED || xa + 3 < L.nx) {
+                if (!idx_ok(qo, 4, L.elems, B.err)) {
+                } else if (!RAGGED || xa + 3 < L.nx) {
                     *reinterpret_cast<float4*>(hi_n + qo) = ho;
                     *reinterpret_cast<uint2*>(lo_n + qo) = lo_encode4(ho, lo);
                     *reinterpret_cast<float4*>(d_out + qo) = dout;
@@ -434,7 +438,7 @@ __device__ __forceinline__ void fused2_block(const CUtensorMap* m_hi, const CUte
                 const long long qo = L.at(xa, y, lo_face ? -1 : L.nz);
 #pragma unroll
                 for (int e = 0; e < 4; ++e)
-                    if (e < nlive) {
+                    if (e < nlive && idx_ok(qo + e, 1, L.elems, B.err)) {
                         hi_n[qo + e] = el(ho, e);
                         lo_n[qo + e] = lo_encode(el(ho, e), el(lo, e));
                     }

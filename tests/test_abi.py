@@ -33,9 +33,23 @@ def test_library_exports_every_declared_symbol(lib_path):
     assert not missing, f"declared but not exported: {missing}"
 
 
+def test_debug_variant_exports_the_same_symbols():
+    """The HG_DEBUG library is the same ABI with index checks compiled in; without a GPU only its exports and its
+    own answer to hg_is_debug_build are checkable."""
+    from paper_1602_05700_gb300.builder import build
+    D = ctypes.CDLL(build(debug=True))
+    missing = [n for n in sorted(_declared()) if not hasattr(D, n)]
+    assert not missing, f"declared but not exported by the debug build: {missing}"
+    assert D.hg_is_debug_build() == 1
+
+
 def test_binding_covers_every_declared_symbol():
     from paper_1602_05700_gb300 import _lib
     assert _declared() == set(_lib.SIGNATURES)
+
+
+def test_release_library_reports_release(lib_path):
+    assert ctypes.CDLL(lib_path).hg_is_debug_build() == 0
 
 
 def test_last_error_is_empty_string_initially(lib_path):
