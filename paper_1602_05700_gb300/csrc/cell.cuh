@@ -11,6 +11,8 @@
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
+#include "lap_int.cuh"
+
 namespace hg {
 
 // ---- storage of the compensation -------------------------------------------------------------------------------
@@ -164,15 +166,30 @@ __device__ __forceinline__ void f32k_update4_scalar(const float4& c, const float
 // each operation rounded separately, in this order -- the plain evaluation of the update.  Every FP64 rounding of
 // the step is thereby fixed by the formula alone, so any IEEE implementation that evaluates it in the same order
 // without contraction produces the same bits.  2c is exact, so 2c - prev is one fused multiply-add with the same
-// single rounding: 15 FP64 instructions.
-__device__ __forceinline__ double f64_update(double xl, double xr, double ys, double yn, double zm, double zp, double c,
-                                             double prev, double s, double nu2) {
+// single rounding: 15 FP64 instructions, of which L takes 11.  Where none of L's 11 operations rounds (the neighbours
+// share c's sign, lie within a binade of it and differ from it by less than 2^50 of its half-ulps -- any smooth
+// field, and the all-zero stencils ahead of a wave front), lap6_int (lap_int.cuh) forms L from integers with the same
+// bits; where prev has c's sign, lies within a binade of it and below 2|c|, twice_minus_int rounds 2c - prev from
+// integers.  That leaves 3 FP64 instructions per cell (nu^2 L, the add, the subtraction of s); a lane outside those
+// conditions evaluates the FP64 operations as written (the two functions below, kept out of line so that the common
+// path does not carry them).
+static __device__ __noinline__ double twice_minus_fp64(double c, double prev) { return __fma_rn(2.0, c, -prev); }
+
+static __device__ __noinline__ double lap6_fp64(double xl, double xr, double ys, double yn, double zm, double zp,
+                                                double c) {
     double L = __dadd_rn(__dsub_rn(xl, c), __dsub_rn(xr, c));
     L = __dadd_rn(L, __dsub_rn(ys, c));
     L = __dadd_rn(L, __dsub_rn(yn, c));
     L = __dadd_rn(L, __dsub_rn(zm, c));
-    L = __dadd_rn(L, __dsub_rn(zp, c));
-    return __dsub_rn(__dadd_rn(__fma_rn(2.0, c, -prev), __dmul_rn(nu2, L)), s);
+    return __dadd_rn(L, __dsub_rn(zp, c));
+}
+
+__device__ __forceinline__ double f64_update(double xl, double xr, double ys, double yn, double zm, double zp, double c,
+                                             double prev, double s, double nu2) {
+    double L, t;
+    if (!lap6_int(c, xl, xr, ys, yn, zm, zp, L)) L = lap6_fp64(xl, xr, ys, yn, zm, zp, c);
+    if (!twice_minus_int(c, prev, t)) t = twice_minus_fp64(c, prev);
+    return __dsub_rn(__dadd_rn(t, __dmul_rn(nu2, L)), s);
 }
 
 // Robin ghost sub-step in FP64 (monopole radiation condition, upwinded) for u = r phi:
