@@ -169,11 +169,17 @@ __device__ __forceinline__ void f32k_update4_scalar(const float4& c, const float
 // single rounding: 15 FP64 instructions, of which L takes 11.  Where none of L's 11 operations rounds (the neighbours
 // share c's sign, lie within a binade of it and differ from it by less than 2^50 of its half-ulps -- any smooth
 // field, and the all-zero stencils ahead of a wave front), lap6_int (lap_int.cuh) forms L from integers with the same
-// bits; where prev has c's sign, lies within a binade of it and below 2|c|, twice_minus_int rounds 2c - prev from
-// integers.  That leaves 3 FP64 instructions per cell (nu^2 L, the add, the subtraction of s); a lane outside those
-// conditions evaluates the FP64 operations as written (the two functions below, kept out of line so that the common
-// path does not carry them).
+// bits; where they differ more but each difference is still exact (neighbours within a factor of 2 of c, as in the
+// steep tails of a compact source), lap6_diffs gives the six differences from integers and only the five additions
+// run in FP64; where prev has c's sign, lies within a binade of it and below 2|c|, twice_minus_int rounds 2c - prev
+// from integers.  That leaves 3 FP64 instructions per cell in smooth regions (nu^2 L, the add, the subtraction of s);
+// a lane outside those conditions evaluates the FP64 operations as written (the functions below, kept out of line so
+// that the common path does not carry them).
 static __device__ __noinline__ double twice_minus_fp64(double c, double prev) { return __fma_rn(2.0, c, -prev); }
+
+static __device__ __noinline__ double sum6_fp64(double d0, double d1, double d2, double d3, double d4, double d5) {
+    return __dadd_rn(__dadd_rn(__dadd_rn(__dadd_rn(__dadd_rn(d0, d1), d2), d3), d4), d5);
+}
 
 static __device__ __noinline__ double lap6_fp64(double xl, double xr, double ys, double yn, double zm, double zp,
                                                 double c) {
@@ -187,7 +193,13 @@ static __device__ __noinline__ double lap6_fp64(double xl, double xr, double ys,
 __device__ __forceinline__ double f64_update(double xl, double xr, double ys, double yn, double zm, double zp, double c,
                                              double prev, double s, double nu2) {
     double L, t;
-    if (!lap6_int(c, xl, xr, ys, yn, zm, zp, L)) L = lap6_fp64(xl, xr, ys, yn, zm, zp, c);
+    if (!lap6_int(c, xl, xr, ys, yn, zm, zp, L)) {
+        double d[6];
+        if (lap6_diffs(c, xl, xr, ys, yn, zm, zp, d))
+            L = sum6_fp64(d[0], d[1], d[2], d[3], d[4], d[5]);
+        else
+            L = lap6_fp64(xl, xr, ys, yn, zm, zp, c);
+    }
     if (!twice_minus_int(c, prev, t)) t = twice_minus_fp64(c, prev);
     return __dsub_rn(__dadd_rn(t, __dmul_rn(nu2, L)), s);
 }

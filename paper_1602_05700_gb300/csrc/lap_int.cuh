@@ -95,6 +95,45 @@ __host__ __device__ __forceinline__ bool lap6_int(double c, double x0, double x1
     return ok && ((ec >= 64u && ec <= 2000u) || (cb == 0ull && A == 0ull));
 }
 
+// The steep regions (neighbours up to a factor of 2 from c, as in the tails of a compact source) fail lap6_int's
+// bound, but there each difference x - c is still exact (Sterbenz: c/2 <= x <= 2c of one sign), only the partial
+// sums round.  lap6_diffs gives the six differences as doubles from integers -- the units of lap6_int, the bound
+// replaced by the Sterbenz condition 2X >= C and X <= 2C -- so that only the five additions remain for the FP64 unit.
+// False (d not set) when some neighbour is outside that condition or c outside the normal range above.
+__host__ __device__ __forceinline__ double pack_units(long long D, unsigned ec, unsigned long long csign) {
+    // D u with u = 2^(e_c - 1076), |D| < 2^54 and exactly representable (at most 53 significant bits)
+    const unsigned long long A = (unsigned long long)(D < 0 ? -D : D);
+    const int lz = clz64(A);
+    const int sh = 11 - lz;
+    const unsigned long long mant = sh > 0 ? A >> sh : A << ((-sh) & 63);
+    const unsigned long long sign = (csign ^ (D < 0 ? (1ull << 63) : 0ull)) & (1ull << 63);
+    return A == 0 ? 0.0 : bits_d(sign | ((((unsigned long long)(ec + 10u - (unsigned)lz) - 1ull) << 52) + mant));
+}
+
+__host__ __device__ __forceinline__ bool lap6_diffs(double c, double x0, double x1, double x2, double x3, double x4,
+                                                    double x5, double (&d)[6]) {
+    const unsigned long long cb = dbits(c);
+    const unsigned hc = (unsigned)(cb >> 52);
+    const unsigned ec = hc & 0x7ffu;
+    const long long C = (long long)(((cb & kFrac52) | kHidden52) << 1);
+    bool ok = ec >= 64u && ec <= 2000u;
+    long long D[6];
+    const double x[6] = {x0, x1, x2, x3, x4, x5};
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        const unsigned long long xb = dbits(x[i]);
+        const unsigned e = (unsigned)(xb >> 52) - hc + 1u;
+        const long long X = (long long)(((xb & kFrac52) | kHidden52) << (e & 3u));
+        ok = ok && e <= 2u && 2 * X >= C && X <= 2 * C;
+        D[i] = X - C;
+    }
+    if (ok) {
+#pragma unroll
+        for (int i = 0; i < 6; ++i) d[i] = pack_units(D[i], ec, cb);
+    }
+    return ok;
+}
+
 // t = 2c - prev rounded once to nearest-even (the leapfrog's first operation), from integers where c is normal in the
 // range above and prev has c's sign, an exponent within one of c's and |prev| < 2|c|: in units u = 2^(e_c - 1076),
 // T = 4 M_c - M_prev 2^(e_prev - e_c + 1) is a positive integer below 2^55, rounded here to 53 significant bits.

@@ -1,6 +1,6 @@
 // Host check of the integer forms in lap_int.cuh (the Laplacian sum and 2c - prev) against the FP64 evaluation order
 // they replace, compiled without contraction: prints "cases accepted mismatches" over seeded random inputs of several
-// kinds (n sextuples and n pairs).
+// kinds (n sextuples through both Laplacian forms and n pairs).
 #include <stdio.h>
 #include <stdlib.h>
 #include <math.h>
@@ -30,7 +30,7 @@ int main(int argc, char** argv) {
     state = argc > 2 ? strtoull(argv[2], 0, 10) : 1;
     long accepted = 0, mismatches = 0, cases = 0;
     for (long t = 0; t < n; ++t) {
-        const int kind = (int)(next_u64() % 10);
+        const int kind = (int)(next_u64() % 11);
         double c, x[6];
         // c: a potential-like value of either sign over many binades, sometimes at a power of two
         c = -(0.01 + unif()) * ldexp(1.0, (int)(next_u64() % 40) - 20);
@@ -50,6 +50,7 @@ int main(int argc, char** argv) {
                 case 6: x[i] = hg::bits_d(hg::dbits(c) + (int64_t)(next_u64() % 2048) - 1024); break;  // ulps of c
                 case 7: x[i] = c * (1.0 + ldexp(r, -(int)(next_u64() % 60))); break;          // near 2^50 units
                 case 8: x[i] = hg::bits_d(hg::dbits(c) + (int64_t)(next_u64() % 64) - 32); break;
+                case 10: x[i] = c * exp(0.8 * r); break;  // steep tail: neighbours up to a factor of 2.2 apart
                 default: {  // quiet region ahead of a front: mostly +0, some -0, subnormals, small normals
                     const int w = (int)(next_u64() % 16);
                     x[i] = w < 11 ? 0.0 : w == 11 ? -0.0 : w == 12 ? 0x1p-1074 * (double)(next_u64() % 5)
@@ -57,17 +58,30 @@ int main(int argc, char** argv) {
                 }
             }
         }
-        double Li = 0.0;
-        const bool ok = hg::lap6_int(c, x[0], x[1], x[2], x[3], x[4], x[5], Li);
-        ++cases;
-        if (!ok) continue;
-        ++accepted;
         const double Lf = lap_fp64(c, x);
-        if (hg::dbits(Li) != hg::dbits(Lf)) {
-            if (mismatches < 5)
-                fprintf(stderr, "mismatch kind %d c=%a x=%a %a %a %a %a %a int=%a fp64=%a\n", kind, c, x[0], x[1], x[2],
-                        x[3], x[4], x[5], Li, Lf);
-            ++mismatches;
+        for (int path = 0; path < 2; ++path) {  // exact-sum path; exact differences summed in FP64
+            double Li = 0.0, d[6];
+            bool ok;
+            if (path == 0) {
+                ok = hg::lap6_int(c, x[0], x[1], x[2], x[3], x[4], x[5], Li);
+            } else {
+                ok = hg::lap6_diffs(c, x[0], x[1], x[2], x[3], x[4], x[5], d);
+                for (int i = 0; ok && i < 6; ++i)
+                    if (hg::dbits(d[i]) != hg::dbits(x[i] - c)) {
+                        if (mismatches < 5) fprintf(stderr, "difference %d: c=%a x=%a int=%a\n", i, c, x[i], d[i]);
+                        ++mismatches;
+                    }
+                Li = ((((d[0] + d[1]) + d[2]) + d[3]) + d[4]) + d[5];
+            }
+            ++cases;
+            if (!ok) continue;
+            ++accepted;
+            if (hg::dbits(Li) != hg::dbits(Lf)) {
+                if (mismatches < 5)
+                    fprintf(stderr, "mismatch path %d kind %d c=%a x=%a %a %a %a %a %a int=%a fp64=%a\n", path, kind, c,
+                            x[0], x[1], x[2], x[3], x[4], x[5], Li, Lf);
+                ++mismatches;
+            }
         }
     }
     // 2c - prev: prev near c (smooth), exactly c, a few ulps away, up to and beyond 2|c|, of either sign, zeros

@@ -1,8 +1,9 @@
 """The FP64 sweep's integer forms (csrc/lap_int.cuh) against the FP64 evaluation order they stand in for, on the host:
-wherever the Laplacian sum accepts a sextuple, or 2c - prev a pair, its bits must equal the plain FP64 order (each
-difference, partial sum and the leapfrog's 2c - prev rounded, no contraction), over seeded random inputs of many
-kinds -- smooth, flat, rough, exact ties and zeros, sign changes, neighbours a few ulps apart (rounding ties),
-differences near the 2^50-unit limit, |prev| near 2|c| and values in every binade."""
+wherever one of the two Laplacian paths (exact sum, rounded sum) accepts a sextuple, or 2c - prev a pair, its bits
+must equal the plain FP64 order (each difference, partial sum and the leapfrog's 2c - prev rounded, no contraction),
+over seeded random inputs of many kinds -- smooth, flat, rough, steep tails, exact ties and zeros, sign changes,
+neighbours a few ulps apart (rounding ties), differences near the 2^50-unit limit, |prev| near 2|c| and values in
+every binade."""
 import os
 import shutil
 import subprocess
@@ -28,5 +29,5 @@ def test_integer_laplacian_equals_fp64_order(checker, seed):
     out = subprocess.run([checker, "4000000", str(seed)], check=True, capture_output=True, text=True)
     cases, accepted, mismatches = map(int, out.stdout.split())
     assert mismatches == 0, out.stderr
-    assert cases == 2 * 4000000  # sextuples for the Laplacian sum, pairs for 2c - prev
-    assert accepted > cases // 2  # most fields take the integer path
+    assert cases == 3 * 4000000  # sextuples through both Laplacian paths, pairs for 2c - prev
+    assert accepted > cases // 2  # most inputs take an integer path
