@@ -271,10 +271,11 @@ int hg_batch_step(hg_batch* b, int n_substeps);
 int hg_batch_info(const hg_batch* b, int* z_planes_per_block, long long* blocks_per_substep);
 /* the whole autotuned launch: out[0] = FP64 z planes per block, out[1] = FP64 tile rows (0: per grid, 128- or
  * 32-cell rows, whichever leaves fewer lanes idle; 4: 128-cell rows for every grid), out[2] = compensated-float
- * (TMA-staged) z planes per block.  The choice is timed on the first sub-steps of the first hg_batch_step and cached
- * per device and set of grids for the life of the process (an autotuner of this library; the
- * paper has no counterpart). */
-int hg_batch_tuning(const hg_batch* b, int out[3]);
+ * (TMA-staged) z planes per block, out[3] = 1 when the two precisions run as separate launches per sub-step (two
+ * independent chains on two streams; 0: one launch holds both).  The choice is timed on the first sub-steps of the
+ * first hg_batch_step and cached per device and set of grids for the life of the process (an autotuner of this
+ * library; the paper has no counterpart). */
+int hg_batch_tuning(const hg_batch* b, int out[4]);
 void hg_batch_free(hg_batch* b);
 
 /*

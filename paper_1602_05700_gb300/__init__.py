@@ -374,11 +374,11 @@ class Batch:
     def info(self):
         zb, nb = ctypes.c_int(), ctypes.c_longlong()
         _lib.check(_lib.lib().hg_batch_info(self._h, ctypes.byref(zb), ctypes.byref(nb)))
-        t = (ctypes.c_int * 3)()
+        t = (ctypes.c_int * 4)()
         _lib.check(_lib.lib().hg_batch_tuning(self._h, t))
         return {"z_planes_per_block": zb.value, "blocks_per_substep": nb.value,
                 "f64_tile_rows": "per grid (128 or 32 cells)" if t[1] == 0 else "128 cells",
-                "f32_z_planes_per_block": t[2]}
+                "f32_z_planes_per_block": t[2], "precisions_in_separate_launches": bool(t[3])}
 
     def free(self):
         if getattr(self, "_h", None) is not None:

@@ -16,8 +16,11 @@
 //     128- and 32-cell rows (1 per lane) leaves fewer lanes idle (a 96-cell row fills 75% of a 128-cell tile; the
 //     FP64 pipe pays for idle lanes, since its rate is per warp instruction);
 //   * the z extent of an FP64 block (8 .. 64 planes: the number of blocks against the share of the z warm-up);
-//   * the z extent of a TMA-staged compensated-float block (8 or 16 planes).
-// All FP64 candidates are timed first (eight), then the two float extents with the best FP64 setting.
+//   * the z extent of a TMA-staged compensated-float block (8 or 16 planes);
+//   * one launch per sub-step for both precisions, or two (split mode: an FP64-only launch and a float-only launch
+//     per sub-step, each with its own sweep's registers and block shape, as two independent chains on two streams).
+// All FP64 candidates are timed first (eight), then the split mode with the best FP64 setting, then the float
+// extent of 16 planes with the better of the two.
 #include <stdio.h>
 #include <string.h>
 
@@ -44,6 +47,13 @@ struct hg_batch {
     int zb;    // FP64 planes per block, 0 until tuned
     int cpl;   // FP64 cells per lane: 0 = per grid, whichever tile row fits better; 4 = 128-cell rows everywhere
     int zb32;  // compensated-float (TMA-staged) planes per block
+    int split; // 1: FP64 and compensated-float entries as two launches per sub-step, on two streams
+    // split mode: the two classes' own prefix tables (FP64 entries first in the table, then the float ones)
+    cudaStream_t stream2;
+    cudaEvent_t ev_fork, ev_join;
+    unsigned* d_first2;  // FP64 prefix (n64 + 1 entries), then float prefix (n32 + 1 entries)
+    int n64, n32;
+    unsigned blocks64, blocks32;
     // graph of `graph_steps` sub-steps
     cudaGraph_t graph;
     cudaGraphExec_t exec;
@@ -54,7 +64,7 @@ namespace {
 
 std::mutex g_tune_mu;
 struct Tuning {
-    int zb, cpl, zb32;
+    int zb, cpl, zb32, split;
 };
 std::map<std::string, Tuning> g_tuned;  // autotuner cache: key -> the chosen launch
 
@@ -112,6 +122,19 @@ int upload_tables(hg_batch* b) {
     b->first.assign(1, 0);
     for (const TmaEntry& e : tab[0]) b->first.push_back(b->first.back() + sweep_blocks(e.A));
     b->total_blocks = b->first.back();
+    // the classes' own prefixes: FP64 entries are [0, n64), float entries [n64, n)
+    b->n64 = 0;
+    for (hg_grid* g : order) b->n64 += g->prec == HG_PREC_F64 ? 1 : 0;
+    b->n32 = b->n - b->n64;
+    std::vector<unsigned> first2;
+    first2.push_back(0);
+    for (int i = 0; i < b->n64; ++i) first2.push_back(first2.back() + sweep_blocks(tab[0][i].A));
+    b->blocks64 = first2.back();
+    first2.push_back(0);
+    for (int i = b->n64; i < b->n; ++i) first2.push_back(first2.back() + sweep_blocks(tab[0][i].A));
+    b->blocks32 = first2.back();
+    HG_CUDA(cudaMemcpyAsync(b->d_first2, first2.data(), first2.size() * sizeof(unsigned), cudaMemcpyHostToDevice,
+                            b->stream));
     for (int p = 0; p < 2; ++p)
         HG_CUDA(cudaMemcpyAsync(b->d_tab[p], tab[p].data(), tab[p].size() * sizeof(TmaEntry), cudaMemcpyHostToDevice,
                                 b->stream));
@@ -121,8 +144,33 @@ int upload_tables(hg_batch* b) {
     return HG_OK;
 }
 
-// the launch of one sub-step of parity p
-int enqueue_substep(hg_batch* b, int p) { return launch_step_batch(b->stream, b->d_tab[p], b->d_first, b->n, b->total_blocks); }
+// the launches of `count` sub-steps, the first of parity p0.  Split mode: the FP64 chain on the batch stream and
+// the float chain on the second stream, forked from and joined back into the batch stream (the chains touch
+// different grids, so they need no ordering between them).
+int enqueue_substeps(hg_batch* b, int p0, int count) {
+    int rc = HG_OK;
+    if (!b->split) {
+        for (int s = 0; s < count && rc == HG_OK; ++s)
+            rc = launch_step_batch(b->stream, b->d_tab[(p0 + s) & 1], b->d_first, b->n, b->total_blocks);
+        return rc;
+    }
+    HG_CUDA(cudaEventRecord(b->ev_fork, b->stream));
+    HG_CUDA(cudaStreamWaitEvent(b->stream2, b->ev_fork, 0));
+    for (int s = 0; s < count && rc == HG_OK; ++s) {
+        const int p = (p0 + s) & 1;
+        rc = launch_batch_class(b->stream, true, b->d_tab[p], b->d_first2, b->n64, b->blocks64);
+        if (rc == HG_OK)
+            rc = launch_batch_class(b->stream2, false, b->d_tab[p] + b->n64, b->d_first2 + b->n64 + 1, b->n32,
+                                    b->blocks32);
+    }
+    // join even after an error, so that a capture in progress ends with both streams in it
+    cudaError_t e1 = cudaEventRecord(b->ev_join, b->stream2);
+    cudaError_t e2 = cudaStreamWaitEvent(b->stream, b->ev_join, 0);
+    if (rc) return rc;
+    if (e1 != cudaSuccess) return cuda_fail(e1, "cudaEventRecord");
+    if (e2 != cudaSuccess) return cuda_fail(e2, "cudaStreamWaitEvent");
+    return HG_OK;
+}
 
 void advance(hg_batch* b, int n) {
     for (hg_grid* g : b->grids) {
@@ -143,6 +191,7 @@ int autotune(hg_batch* b, int budget, int* taken) {
             b->zb = it->second.zb;
             b->cpl = it->second.cpl;
             b->zb32 = it->second.zb32;
+            b->split = it->second.split;
             return upload_tables(b);
         }
     }
@@ -154,9 +203,9 @@ int autotune(hg_batch* b, int budget, int* taken) {
     std::vector<Tuning> cand;
     if (any64)
         for (int cpl : {0, 4})
-            for (int zb : {8, 16, 32, 64}) cand.push_back({zb, cpl, 8});
+            for (int zb : {8, 16, 32, 64}) cand.push_back({zb, cpl, 8, 0});
     else
-        cand.push_back({8, 0, 8});
+        cand.push_back({8, 0, 8, 0});
     Tuning best = cand[0];
     float best_ms = -1.f;
     cudaEvent_t e0, e1;
@@ -172,10 +221,10 @@ int autotune(hg_batch* b, int budget, int* taken) {
         b->zb = t.zb;
         b->cpl = t.cpl;
         b->zb32 = t.zb32;
+        b->split = t.split;
         if ((rc = upload_tables(b))) return false;
         cudaEventRecord(e0, b->stream);
-        if ((rc = enqueue_substep(b, 0))) return false;  // two sub-steps (both parities) per candidate
-        if ((rc = enqueue_substep(b, 1))) return false;
+        if ((rc = enqueue_substeps(b, 0, 2))) return false;  // two sub-steps (both parities) per candidate
         cudaEventRecord(e1, b->stream);
         cudaError_t e = cudaEventSynchronize(e1);
         if (e != cudaSuccess) {
@@ -194,6 +243,11 @@ int autotune(hg_batch* b, int budget, int* taken) {
     };
     for (const Tuning& t : cand)
         if (!time_one(t)) break;
+    if (rc == HG_OK && complete && best_ms >= 0.f) {  // each precision class as a launch of its own
+        Tuning t = best;
+        t.split = 1;
+        time_one(t);
+    }
     if (rc == HG_OK && complete && any32 && best_ms >= 0.f) {
         Tuning t = best;
         t.zb32 = 16;
@@ -206,11 +260,13 @@ int autotune(hg_batch* b, int budget, int* taken) {
         b->zb = 8;
         b->cpl = 0;
         b->zb32 = 8;
+        b->split = 0;
         return upload_tables(b);
     }
     b->zb = best.zb;
     b->cpl = best.cpl;
     b->zb32 = best.zb32;
+    b->split = best.split;
     if (complete) {
         std::lock_guard<std::mutex> lock(g_tune_mu);
         g_tuned[key] = best;
@@ -228,12 +284,14 @@ void destroy_graph(hg_batch* b) {
 
 void release(hg_batch* b) {
     destroy_graph(b);
-    void* ptrs[] = {b->d_tab[0], b->d_tab[1], b->d_first};
+    void* ptrs[] = {b->d_tab[0], b->d_tab[1], b->d_first, b->d_first2};
     for (void* p : ptrs)
         if (p) cudaFree(p);
-    if (b->ev_in) cudaEventDestroy(b->ev_in);
-    if (b->ev_out) cudaEventDestroy(b->ev_out);
+    cudaEvent_t evs[] = {b->ev_in, b->ev_out, b->ev_fork, b->ev_join};
+    for (cudaEvent_t ev : evs)
+        if (ev) cudaEventDestroy(ev);
     if (b->stream) cudaStreamDestroy(b->stream);
+    if (b->stream2) cudaStreamDestroy(b->stream2);
 }
 
 }  // namespace
@@ -264,10 +322,12 @@ int hg_batch_create(hg_grid* const* grids, int n, hg_batch** out) {
         if (rc == HG_OK && err != cudaSuccess) rc = cuda_fail(err, what);
     };
     ck(cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking), "cudaStreamCreate");
-    ck(cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming), "cudaEventCreate");
-    ck(cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming), "cudaEventCreate");
+    ck(cudaStreamCreateWithFlags(&b->stream2, cudaStreamNonBlocking), "cudaStreamCreate");
+    for (cudaEvent_t* ev : {&b->ev_in, &b->ev_out, &b->ev_fork, &b->ev_join})
+        ck(cudaEventCreateWithFlags(ev, cudaEventDisableTiming), "cudaEventCreate");
     for (int p = 0; p < 2 && rc == HG_OK; ++p) ck(cudaMalloc(&b->d_tab[p], n * sizeof(TmaEntry)), "cudaMalloc(table)");
     ck(cudaMalloc(&b->d_first, (n + 1) * sizeof(unsigned)), "cudaMalloc(table)");
+    ck(cudaMalloc(&b->d_first2, (n + 2) * sizeof(unsigned)), "cudaMalloc(table)");
     if (rc == HG_OK) rc = upload_tables(b);
     if (rc != HG_OK) {
         release(b);
@@ -302,7 +362,7 @@ int hg_batch_step(hg_batch* b, int n_substeps) {
         if (b->graph_steps != n) {
             destroy_graph(b);
             HG_CUDA(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
-            for (int s = 0; s < n && rc == HG_OK; ++s) rc = enqueue_substep(b, s & 1);
+            rc = enqueue_substeps(b, 0, n);
             cudaGraph_t graph = nullptr;
             e = cudaStreamEndCapture(b->stream, &graph);
             if (rc) {
@@ -330,12 +390,13 @@ int hg_batch_info(const hg_batch* b, int* z_planes_per_block, long long* blocks_
     return HG_OK;
 }
 
-int hg_batch_tuning(const hg_batch* b, int out[3]) {
+int hg_batch_tuning(const hg_batch* b, int out[4]) {
     HG_RANGE("hg_batch_tuning");
     if (!b || !out) return fail(HG_ERR_ARG, "null argument");
     out[0] = b->zb;
     out[1] = b->cpl;
     out[2] = b->zb32;
+    out[3] = b->split;
     return HG_OK;
 }
 

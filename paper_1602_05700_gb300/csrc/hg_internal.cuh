@@ -299,6 +299,9 @@ struct alignas(128) TmaEntry {
 };
 int tma_entry(hg_grid* g, TmaEntry* e, int zb = 0);  // compensated-float g's sub-step cur -> 1 - cur (all ghosts in the launch)
 int launch_step_batch(cudaStream_t st, const TmaEntry* tab, const unsigned* first, int n, unsigned total_blocks);
+// one precision class of a batched sub-step (FP64 entries, or compensated-float entries) as a launch of its own
+int launch_batch_class(cudaStream_t st, bool f64, const TmaEntry* tab, const unsigned* first, int n,
+                       unsigned total_blocks);
 unsigned sweep_blocks(const SweepArgs& A);
 
 // ---- deterministic reductions --------------------------------------------------------------------------------

@@ -424,6 +424,19 @@ __global__ void __launch_bounds__(32 * WY, 2) k_step_f64(const SweepArgs A) {
     sweep_f64_any<WY>(A, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
+// entry of block b in a prefix table of n entries
+__device__ __forceinline__ int batch_entry(const unsigned* __restrict__ first, int n, unsigned b) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(first + mid) <= b)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
 // One launch for the sub-step of many grids: block b belongs to the entry e with first[e] <= b < first[e+1]
 // (binary search in the prefix table).  Compensated-float entries run the TMA-staged sweep (their tensor maps live in
 // the table, in global memory; the issuing thread acquires them through the tensormap proxy before its first copy),
@@ -435,14 +448,7 @@ __global__ void __launch_bounds__(32 * (WY + 1), 2) k_step_batch(const TmaEntry*
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ __align__(8) unsigned long long bars[2 * S];
     const unsigned b = blockIdx.x;
-    int lo = 0, hi = n - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (__ldg(first + mid) <= b)
-            lo = mid;
-        else
-            hi = mid - 1;
-    }
+    const int lo = batch_entry(first, n, b);
     const TmaEntry& E = tab[lo];
     const unsigned local = b - __ldg(first + lo);
     const int bx = (int)(local % E.A.gx), by = (int)((local / E.A.gx) % E.A.gy), bz = (int)(local / (E.A.gx * E.A.gy));
@@ -454,6 +460,34 @@ __global__ void __launch_bounds__(32 * (WY + 1), 2) k_step_batch(const TmaEntry*
     } else {
         sweep_f64_any<WY>(E.A, bx, by, bz);
     }
+}
+
+// The two halves of a batched sub-step as launches of their own (the split mode of the batch): compensated-float
+// entries only, with the single-grid TMA sweep's launch shape (3 blocks per SM), and FP64 entries only, with the
+// single-grid FP64 sweep's (8 warps, 2 blocks per SM).  Each half gets the registers of its own sweep instead of the
+// larger of the two.
+template <int WY, int S>
+__global__ void __launch_bounds__(32 * (WY + 1), 3) k_batch_tma(const TmaEntry* __restrict__ tab,
+                                                                const unsigned* __restrict__ first, int n) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ __align__(8) unsigned long long bars[2 * S];
+    const int e = batch_entry(first, n, blockIdx.x);
+    const TmaEntry& E = tab[e];
+    const unsigned local = blockIdx.x - __ldg(first + e);
+    const int bx = (int)(local % E.A.gx), by = (int)((local / E.A.gx) % E.A.gy), bz = (int)(local / (E.A.gx * E.A.gy));
+    if (threadIdx.y == WY && threadIdx.x == 0)
+        for (int m = 0; m < 4; ++m)
+            asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&E.m[m]) : "memory");
+    tma_sweep<WY, S>(&E.m[0], &E.m[1], &E.m[2], &E.m[3], E.A, bx, by, bz, E.err, smem, bars);
+}
+
+template <int WY>
+__global__ void __launch_bounds__(32 * WY, 2) k_batch_f64(const TmaEntry* __restrict__ tab,
+                                                          const unsigned* __restrict__ first, int n) {
+    const int e = batch_entry(first, n, blockIdx.x);
+    const SweepArgs& A = tab[e].A;
+    const unsigned local = blockIdx.x - __ldg(first + e);
+    sweep_f64_any<WY>(A, (int)(local % A.gx), (int)((local / A.gx) % A.gy), (int)(local / (A.gx * A.gy)));
 }
 
 }  // namespace
@@ -528,6 +562,23 @@ int launch_step_single(hg_grid* g) {
         k_ghosts_periodic<<<(unsigned)((A.B.off[6] - t0p + 255) / 256), 256, 0, g->stream>>>(A, t0p);
         HG_LAUNCHED("periodic ghost kernel");
     }
+    return HG_OK;
+}
+
+int launch_batch_class(cudaStream_t st, bool f64, const TmaEntry* tab, const unsigned* first, int n,
+                       unsigned total_blocks) {
+    if (n < 1 || total_blocks == 0) return HG_OK;
+    if (f64) {
+        k_batch_f64<kWY><<<total_blocks, dim3(32, kWY), 0, st>>>(tab, first, n);
+    } else {
+        static unsigned long long attr_done = 0;
+        const int smem = kStages * StageGeom<kTmaWY>::bytes;
+        int rc = smem_attr_once((const void*)k_batch_tma<kTmaWY, kStages>, smem, &attr_done);
+        if (rc) return rc;
+        k_batch_tma<kTmaWY, kStages><<<total_blocks, dim3(32, kTmaWY + 1), smem, st>>>(tab, first, n);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, f64 ? "batched FP64 sub-step kernel" : "batched float sub-step kernel");
     return HG_OK;
 }
 
