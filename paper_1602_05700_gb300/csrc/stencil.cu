@@ -2,23 +2,25 @@
 //
 //   phi^{n+1} = 2 phi^n - phi^{n-1} + nu^2 sum_{6 nb}(phi^n_nb - phi^n) - s,   s = (c_h dt)^2 4 pi G rho
 //
-// over the interior of the padded layout (ghosts are filled by boundary.cu).  One kernel per precision:
+// over the interior of the padded layout.  This file holds the FP64 sweep, the small ghost kernels of a single
+// grid's sub-step, the batched launches of many grids, and the host side of a single grid's sub-step; the
+// compensated-float sweep itself is the TMA-staged kernel of stencil_tma.cu / sweep_tma.cuh.
 //
 // * f32k: float storage with compensated increments.  State per cell: hi + lo = phi^n (a float and its
 //   rounding remainder, stored as a 16-bit code, cell.cuh) and dlt = phi^n - phi^{n-1}.  The sub-step is
 //       dlt' = dlt + (nu^2 (L(hi) + L(lo)) - s),   (hi', lo') = hi + (lo + dlt')  by Fast2Sum,
 //   so phi keeps ~36 bits: 24 bytes of HBM traffic per cell (read hi 4, lo 2, dlt 4, s 4; write hi' 4, lo' 2,
 //   dlt' 4).  hi/lo ping-pong between two buffers (neighbours are read), dlt is updated in place.
-// * f64: double storage, phi^{n+1} written over phi^{n-1}: 32 bytes per cell.  GB300 issues few FP64
-//   instructions per clock (~0.5 T/s), and the update takes 15 of them (cell.cuh), so this kernel is bound by the
-//   FP64 pipe, not by HBM.
+// * f64: double storage, phi^{n+1} written over phi^{n-1}: 32 bytes per cell.  The update's 15 FP64 operations
+//   (cell.cuh) run partly in integer instructions with the same bits (lap_int.cuh); GB300's FP64 rate and the
+//   integer issue bound the kernel, not HBM.
 // The stored "rho" array holds the scaled source s = (c_h dt)^2 4 pi G (rho - rho_bar).
 //
-// Work mapping (both kernels): a warp owns one y-row of 128 consecutive x cells (4 per lane, one 16-byte access
-// per lane for float, two for double) and marches in z through a chunk of planes.  The -z / centre / +z planes
-// are a register queue; x neighbours come from the adjacent lanes by warp shuffles (the two warp-edge cells
-// load one scalar each); y neighbours are the rows of the sibling warps, read through L1.  Ragged tails in x, y
-// and z are masked (lanes beyond nx store nothing; the vector reads of the last group stay inside the padded row).
+// FP64 work mapping: a warp owns one y-row of 128 (or 32) consecutive x cells (4 or 1 per lane, two 16-byte accesses
+// or one 8-byte access per lane) and marches in z through a chunk of planes.  The -z / centre / +z planes are a
+// register queue; x neighbours come from the adjacent lanes by warp shuffles (the two warp-edge cells load one
+// scalar each); y neighbours are the rows of the sibling warps, read through L1.  Ragged tails in x, y and z are
+// masked (lanes beyond nx store nothing; the vector reads of the last group stay inside the padded row).
 #include "cell.cuh"
 #include "hg_internal.cuh"
 #include "sweep_f32k.cuh"
@@ -28,11 +30,6 @@ namespace hg {
 
 namespace {
 
-__device__ __forceinline__ float4 ld4(const float* p) { return __ldg(reinterpret_cast<const float4*>(p)); }
-__device__ __forceinline__ uint2 ldl4(const lo_t* p) { return __ldg(reinterpret_cast<const uint2*>(p)); }
-__device__ __forceinline__ void stl4(lo_t* p, uint2 v) { *reinterpret_cast<uint2*>(p) = v; }
-__device__ __forceinline__ float4 ld4rw(const float* p) { return *reinterpret_cast<const float4*>(p); }
-__device__ __forceinline__ void st4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
 __device__ __forceinline__ double2 ld2(const double* p) { return __ldg(reinterpret_cast<const double2*>(p)); }
 __device__ __forceinline__ double2 ld2rw(const double* p) { return *reinterpret_cast<const double2*>(p); }
 __device__ __forceinline__ void st2(double* p, double2 v) { *reinterpret_cast<double2*>(p) = v; }
@@ -107,109 +104,6 @@ __device__ __forceinline__ void block_face_ghosts(const Layout& L, const Bnd& B,
             const int i = x0 + t % xn, j = j0 + t / xn;
             qg = L.at(i, j, L.nz), qi = qg - L.plane, r = B.off[5] + (long long)j * L.nx + i;
         }, upd);
-}
-
-template <int WY>
-__device__ __forceinline__ void sweep_f32k(const SweepArgs& A, int bx, int by, int bz) {
-    const float* __restrict__ hi_c = (const float*)A.hi_c;
-    const lo_t* __restrict__ lo_c = (const lo_t*)A.lo_c;
-    float* __restrict__ hi_n = (float*)A.hi_n;
-    lo_t* __restrict__ lo_n = (lo_t*)A.lo_n;
-    float* __restrict__ dlt = (float*)A.dlt;
-    const float* __restrict__ rho = (const float*)A.rho;
-    const Layout& L = A.L;
-    const Bnd& B = A.B;
-    const float nu2 = A.nu2f;
-    const int zb = A.zb;
-    const int lane = threadIdx.x;
-    const int j = by * WY + threadIdx.y;
-    const int i0 = bx * 128 + lane * 4;
-    const bool active = i0 < L.nx;  // this lane owns cells
-    const bool halo = i0 <= L.nx;   // this lane's group holds cells or the +x ghost (read for its left neighbour)
-    const int k0 = bz * zb;
-    const int k1 = min(L.nz, k0 + zb);
-    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (j < L.ny && (int)threadIdx.y < WY) {  // rows past ny (or extra warps) only join the epilogue
-    long long q = L.at(i0, j, k0);
-    float4 hm = z4, hc = z4, lm = z4, lc = z4;
-    if (halo) {
-        hm = ld4(hi_c + q - L.plane);
-        lm = lo_decode4(hm, ldl4(lo_c + q - L.plane));
-        hc = ld4(hi_c + q);
-        lc = lo_decode4(hc, ldl4(lo_c + q));
-    }
-    for (int k = k0; k < k1; ++k, q += L.plane) {
-        float4 hp = z4, lp = z4, hs = z4, hn = z4, ls = z4, ln = z4, d = z4, r = z4;
-        float hl = 0.f, hr = 0.f, ll = 0.f, lr = 0.f;
-        if (halo) {
-            hp = ld4(hi_c + q + L.plane);
-            lp = lo_decode4(hp, ldl4(lo_c + q + L.plane));
-        }
-        if (active) {
-            hs = ld4(hi_c + q - L.pitch);
-            hn = ld4(hi_c + q + L.pitch);
-            ls = lo_decode4(hs, ldl4(lo_c + q - L.pitch));
-            ln = lo_decode4(hn, ldl4(lo_c + q + L.pitch));
-            d = ld4rw(dlt + q);
-            r = ld4(rho + q);
-            if (lane == 0) {
-                hl = __ldg(hi_c + q - 1);
-                ll = lo_decode(hl, lo_c[q - 1]);
-            }
-            if (lane == 31 && i0 + 4 <= L.nx) {
-                hr = __ldg(hi_c + q + 4);
-                lr = lo_decode(hr, lo_c[q + 4]);
-            }
-        }
-        float shl = __shfl_up_sync(0xffffffffu, hc.w, 1), sll = __shfl_up_sync(0xffffffffu, lc.w, 1);
-        float shr = __shfl_down_sync(0xffffffffu, hc.x, 1), slr = __shfl_down_sync(0xffffffffu, lc.x, 1);
-        if (lane != 0) {
-            hl = shl;
-            ll = sll;
-        }
-        if (lane != 31) {
-            hr = shr;
-            lr = slr;
-        }
-        if (active)
-            group_update_store(L, B, nu2, i0, q, hc, lc, hl, ll, hr, lr, hs, hn, ls, ln, hm, hp, lm, lp, d, r,
-                               hi_n, lo_n, dlt);
-        hm = hc;
-        hc = hp;
-        lm = lc;
-        lc = lp;
-    }
-    }
-    if (B.faces)
-        block_face_ghosts(L, B, bx * 128, by * WY, WY, k0, k1, bx, by, A.gx, A.gy, [&](const GhostBatch& gb) {
-            float hg[kGB], lg[kGB], hin[kGB], lin[kGB];
-            float2 ab[kGB];
-#pragma unroll
-            for (int u = 0; u < kGB; ++u)
-                if (u < gb.n) {
-                    ab[u] = B.robin32[gb.t[u]];
-                    hg[u] = __ldg(hi_c + gb.qg[u]);
-                    lg[u] = lo_decode(hg[u], lo_c[gb.qg[u]]);
-                    hin[u] = __ldg(hi_c + gb.qi[u]);
-                    lin[u] = lo_decode(hin[u], lo_c[gb.qi[u]]);
-                }
-#pragma unroll
-            for (int u = 0; u < kGB; ++u)
-                if (u < gb.n) {
-                    float gh, gl;
-                    robin_update_f32k(ab[u].x, ab[u].y, hg[u], lg[u], hin[u], lin[u], gh, gl);
-                    hi_n[gb.qg[u]] = gh;
-                    lo_n[gb.qg[u]] = lo_encode(gh, gl);
-                }
-        });
-    if (B.periodic) {
-        __syncthreads();
-        block_periodic_copies(L, bx * 128, by * WY, WY, k0, k1, bx, by, A.gx, A.gy, block_tid(), block_nth(),
-                              [&](long long q, long long d) {
-            hi_n[d] = hi_n[q];
-            lo_n[d] = lo_n[q];
-        });
-    }
 }
 
 // f64: C = 4 cells per lane (two double2 accesses) or C = 1 (one double); arithmetic in cell.cuh
