@@ -318,7 +318,8 @@ def run_ours(args, rank, world, local_rank):
     # end to end through the public API: each step's density from pinned host memory, -grad phi back to pinned
     # host memory, with the copies of one step overlapping the sub-steps of the next (hg_io_step / hg_io_wait)
     if not args.skip_e2e:
-        ke, we = max(4, steps), 2  # the whole run of steps, as the device-resident measurement
+        ke, we = max(4, steps), IO_SETS  # the whole run of steps, as the device-resident measurement; the warm-up
+        # uses every host buffer set once
         # a rotation of four page-locked host buffers for the density and four sets for -grad phi, as a driver with
         # three steps in flight keeps them (each buffer is rewritten only after hg_io_wait has released it): the
         # densities of this workload are analytic in time, so a step's input does not wait for the previous output
