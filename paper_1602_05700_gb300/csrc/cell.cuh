@@ -168,21 +168,14 @@ __device__ __forceinline__ void f32k_update4_scalar(const float4& c, const float
 // without contraction produces the same bits.  2c is exact, so 2c - prev is one fused multiply-add with the same
 // single rounding: 15 FP64 instructions, of which L takes 11.  Where none of L's 11 operations rounds (the neighbours
 // share c's sign, lie within a binade of it and differ from it by less than 2^50 of its half-ulps -- any smooth
-// field, and the all-zero stencils ahead of a wave front), lap6_int (lap_int.cuh) forms L from integers with the same
-// bits; where they differ more but each difference is still exact (neighbours within a factor of 2 of c, as in the
-// steep tails of a compact source), lap6_diffs gives the six differences from integers and only the five additions
-// run in FP64; where prev has c's sign, lies within a binade of it and below 2|c|, twice_minus_int rounds 2c - prev
-// from integers.  That leaves 3 FP64 instructions per cell in smooth regions (nu^2 L, the add, the subtraction of s);
-// a lane outside those conditions evaluates the FP64 operations as written (the functions below, kept out of line so
-// that the common path does not carry them).
-static __device__ __noinline__ double twice_minus_fp64(double c, double prev) { return __fma_rn(2.0, c, -prev); }
-
-static __device__ __noinline__ double sum6_fp64(double d0, double d1, double d2, double d3, double d4, double d5) {
-    return __dadd_rn(__dadd_rn(__dadd_rn(__dadd_rn(__dadd_rn(d0, d1), d2), d3), d4), d5);
-}
-
-static __device__ __noinline__ double lap6_fp64(double xl, double xr, double ys, double yn, double zm, double zp,
-                                                double c) {
+// field, and the all-zero stencils ahead of a wave front), L is the integer sum of the six differences (lap_int.cuh,
+// lap6_exact_sum / pack_units) with the same bits; where they differ more but each difference is still exact
+// (neighbours within a factor of 2 of c, as in the steep tails of a compact source), the six differences come from
+// integers (lap_diff) and only the five additions run in FP64; where prev has c's sign, lies within a binade of it
+// and below 2|c|, twice_minus_int rounds 2c - prev from integers.  That leaves 3 FP64 instructions per cell in smooth
+// regions (nu^2 L, the add, the subtraction of s); outside those conditions the FP64 operations run as written.
+__device__ __forceinline__ double lap6_fp64(double xl, double xr, double ys, double yn, double zm, double zp,
+                                            double c) {
     double L = __dadd_rn(__dsub_rn(xl, c), __dsub_rn(xr, c));
     L = __dadd_rn(L, __dsub_rn(ys, c));
     L = __dadd_rn(L, __dsub_rn(yn, c));
@@ -190,17 +183,53 @@ static __device__ __noinline__ double lap6_fp64(double xl, double xr, double ys,
     return __dadd_rn(L, __dsub_rn(zp, c));
 }
 
+// Out-of-line FP64 forms for the per-lane choice: a lane that needs one calls it, and the common path carries none
+// of its FP64 instructions.
+static __device__ __noinline__ double sum6_ool(double d0, double d1, double d2, double d3, double d4, double d5) {
+    return __dadd_rn(__dadd_rn(__dadd_rn(__dadd_rn(__dadd_rn(d0, d1), d2), d3), d4), d5);
+}
+static __device__ __noinline__ double lap6_ool(double xl, double xr, double ys, double yn, double zm, double zp,
+                                               double c) {
+    return lap6_fp64(xl, xr, ys, yn, zm, zp, c);
+}
+static __device__ __noinline__ double twice_minus_ool(double c, double prev) { return __fma_rn(2.0, c, -prev); }
+
+// WARP_UNIFORM: the form is chosen per warp (the cheapest form every lane of the warp can take), so that a warp never
+// executes two forms one after the other -- the batched launches, whose small grids mix the forms within a warp;
+// otherwise per lane, the slower forms out of line -- the single-grid sweep, measured faster that way on a 512^3
+// grid.  Each form gives every lane the same bits.
+template <bool WARP_UNIFORM>
 __device__ __forceinline__ double f64_update(double xl, double xr, double ys, double yn, double zm, double zp, double c,
                                              double prev, double s, double nu2) {
     double L, t;
-    if (!lap6_int(c, xl, xr, ys, yn, zm, zp, L)) {
-        double d[6];
-        if (lap6_diffs(c, xl, xr, ys, yn, zm, zp, d))
-            L = sum6_fp64(d[0], d[1], d[2], d[3], d[4], d[5]);
-        else
+    const Lap6Sum k = lap6_exact_sum(c, xl, xr, ys, yn, zm, zp);
+    if (WARP_UNIFORM) {
+        const unsigned m = __activemask();
+        if (__all_sync(m, k.exact)) {
+            L = pack_units(k.S, c);
+        } else if (__all_sync(m, lap6_exact_diffs(c, xl, xr, ys, yn, zm, zp))) {
+            L = __dadd_rn(lap_diff(xl, c), lap_diff(xr, c));
+            L = __dadd_rn(L, lap_diff(ys, c));
+            L = __dadd_rn(L, lap_diff(yn, c));
+            L = __dadd_rn(L, lap_diff(zm, c));
+            L = __dadd_rn(L, lap_diff(zp, c));
+        } else {
             L = lap6_fp64(xl, xr, ys, yn, zm, zp, c);
+        }
+        const bool ti = twice_minus_int(c, prev, t);
+        if (!__all_sync(m, ti)) t = __fma_rn(2.0, c, -prev);
+    } else {
+        if (k.exact) {
+            L = pack_units(k.S, c);
+        } else {
+            double d[6];
+            if (lap6_diffs(c, xl, xr, ys, yn, zm, zp, d))
+                L = sum6_ool(d[0], d[1], d[2], d[3], d[4], d[5]);
+            else
+                L = lap6_ool(xl, xr, ys, yn, zm, zp, c);
+        }
+        if (!twice_minus_int(c, prev, t)) t = twice_minus_ool(c, prev);
     }
-    if (!twice_minus_int(c, prev, t)) t = twice_minus_fp64(c, prev);
     return __dsub_rn(__dadd_rn(t, __dmul_rn(nu2, L)), s);
 }
 

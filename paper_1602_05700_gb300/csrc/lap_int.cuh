@@ -58,78 +58,118 @@ __host__ __device__ __forceinline__ int clz64(unsigned long long v) {
 #endif
 }
 
-// one neighbour's term: adds X - C to S, clears ok unless the term meets the conditions above
-__host__ __device__ __forceinline__ void lap_term(double x, unsigned hc, long long C, long long& S, bool& ok) {
+// The steep regions (neighbours up to a factor of 2 from c, as in the tails of a compact source) fail the 2^50 bound,
+// but there each difference x - c is still exact (Sterbenz: c/2 <= x <= 2c of one sign), only the partial sums
+// round: the six differences come from integers -- the same units, the bound replaced by the Sterbenz condition
+// 2X >= C and X <= 2C -- and only the five additions remain for the FP64 unit.
+//
+// lap6_exact_sum evaluates the first condition (every operation of L exact; its S is then L in units of u) and
+// lap6_exact_diffs the second (every difference exact), each in one pass over the six neighbours.  A stencil that
+// passes the first passes the second, and a stencil of seven +0 passes both (L = +0, every difference +0).
+struct Lap6Sum {
+    long long S;  // sum of the six differences in units u = 2^(e_c - 1076), meaningful when exact
+    bool exact;
+};
+
+__host__ __device__ __forceinline__ long long lap_units(double x, unsigned hc, long long C, unsigned& d) {
     const unsigned long long xb = dbits(x);
-    const unsigned d = (unsigned)(xb >> 52) - hc + 1u;  // 0, 1, 2: c's sign and exponent e_c - 1 .. e_c + 1
-    const long long X = (long long)(((xb & kFrac52) | kHidden52) << (d & 3u));
-    const long long D = X - C;
-    ok = ok && d <= 2u && (unsigned long long)(D + (1ll << 50)) < (1ull << 51);
-    S += D;
+    d = (unsigned)(xb >> 52) - hc + 1u;  // 0, 1, 2: c's sign and exponent e_c - 1 .. e_c + 1
+    return (long long)(((xb & kFrac52) | kHidden52) << (d & 3u));
 }
 
-// L as above from integers; false when some operation of the FP64 order might round (then L is not set)
-__host__ __device__ __forceinline__ bool lap6_int(double c, double x0, double x1, double x2, double x3, double x4,
-                                                  double x5, double& L) {
+// c normal in the range above, or c = +0 with six +0 neighbours (c = +0: its terms pass only for neighbours +0,
+// D = 0, or positive subnormals, D > 0, so S = 0 means every neighbour is +0 -- the quiet regions ahead of a front)
+__host__ __device__ __forceinline__ bool lap_c_ok(unsigned long long cb, long long S) {
+    const unsigned ec = (unsigned)(cb >> 52) & 0x7ffu;
+    return (ec >= 64u && ec <= 2000u) || (cb == 0ull && S == 0);
+}
+
+__host__ __device__ __forceinline__ Lap6Sum lap6_exact_sum(double c, double x0, double x1, double x2, double x3,
+                                                           double x4, double x5) {
     const unsigned long long cb = dbits(c);
     const unsigned hc = (unsigned)(cb >> 52);  // sign and biased exponent of c
-    const unsigned ec = hc & 0x7ffu;
-    bool ok = true;
     const long long C = (long long)(((cb & kFrac52) | kHidden52) << 1);
+    const double x[6] = {x0, x1, x2, x3, x4, x5};
+    bool ok = true;
     long long S = 0;
-    lap_term(x0, hc, C, S, ok);
-    lap_term(x1, hc, C, S, ok);
-    lap_term(x2, hc, C, S, ok);
-    lap_term(x3, hc, C, S, ok);
-    lap_term(x4, hc, C, S, ok);
-    lap_term(x5, hc, C, S, ok);
-    // S u with u = 2^(e_c - 1076): |S| = mant 2^-(lz - 11), mant in [2^52, 2^53), biased exponent e_c + 10 - lz
-    const unsigned long long A = (unsigned long long)(S < 0 ? -S : S);
-    const int lz = clz64(A);
-    const unsigned long long sign = (cb ^ (S < 0 ? (1ull << 63) : 0ull)) & (1ull << 63);
-    const unsigned long long mant = A << ((lz - 11) & 63);
-    const unsigned long long e = (unsigned long long)(ec + 10u - (unsigned)lz);
-    L = A == 0 ? 0.0 : bits_d(sign | (((e - 1ull) << 52) + mant));
-    // c = +0: its terms pass only for neighbours +0 (D = 0) or positive subnormals (D > 0), so S = 0 means every
-    // neighbour is +0 and L = +0 (the quiet regions ahead of a wave front)
-    return ok && ((ec >= 64u && ec <= 2000u) || (cb == 0ull && A == 0ull));
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        unsigned d;
+        const long long D = lap_units(x[i], hc, C, d) - C;
+        ok = ok && d <= 2u && (unsigned long long)(D + (1ll << 50)) < (1ull << 51);
+        S += D;
+    }
+    return {S, ok && lap_c_ok(cb, S)};
 }
 
-// The steep regions (neighbours up to a factor of 2 from c, as in the tails of a compact source) fail lap6_int's
-// bound, but there each difference x - c is still exact (Sterbenz: c/2 <= x <= 2c of one sign), only the partial
-// sums round.  lap6_diffs gives the six differences as doubles from integers -- the units of lap6_int, the bound
-// replaced by the Sterbenz condition 2X >= C and X <= 2C -- so that only the five additions remain for the FP64 unit.
-// False (d not set) when some neighbour is outside that condition or c outside the normal range above.
-__host__ __device__ __forceinline__ double pack_units(long long D, unsigned ec, unsigned long long csign) {
-    // D u with u = 2^(e_c - 1076), |D| < 2^54 and exactly representable (at most 53 significant bits)
-    const unsigned long long A = (unsigned long long)(D < 0 ? -D : D);
+__host__ __device__ __forceinline__ bool lap6_exact_diffs(double c, double x0, double x1, double x2, double x3,
+                                                          double x4, double x5) {
+    const unsigned long long cb = dbits(c);
+    const unsigned hc = (unsigned)(cb >> 52);
+    const long long C = (long long)(((cb & kFrac52) | kHidden52) << 1);
+    const double x[6] = {x0, x1, x2, x3, x4, x5};
+    bool ok = true;
+    long long S = 0;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        unsigned d;
+        const long long X = lap_units(x[i], hc, C, d);
+        ok = ok && d <= 2u && 2 * X >= C && X <= 2 * C;
+        S += X - C;
+    }
+    return ok && lap_c_ok(cb, S);
+}
+
+// S u with u = 2^(e_c - 1076), |S| < 2^54 with at most 53 significant bits: |S| = mant 2^-(lz - 11), mant in
+// [2^52, 2^53), biased exponent e_c + 10 - lz; the sign is c's times S's; 0 gives +0
+__host__ __device__ __forceinline__ double pack_units(long long S, double c) {
+    const unsigned long long cb = dbits(c);
+    const unsigned ec = (unsigned)(cb >> 52) & 0x7ffu;
+    const unsigned long long A = (unsigned long long)(S < 0 ? -S : S);
     const int lz = clz64(A);
     const int sh = 11 - lz;
     const unsigned long long mant = sh > 0 ? A >> sh : A << ((-sh) & 63);
-    const unsigned long long sign = (csign ^ (D < 0 ? (1ull << 63) : 0ull)) & (1ull << 63);
+    const unsigned long long sign = (cb ^ (S < 0 ? (1ull << 63) : 0ull)) & (1ull << 63);
     return A == 0 ? 0.0 : bits_d(sign | ((((unsigned long long)(ec + 10u - (unsigned)lz) - 1ull) << 52) + mant));
 }
 
+// x - c from integers (valid when the stencil passed exact_diffs)
+__host__ __device__ __forceinline__ double lap_diff(double x, double c) {
+    const unsigned long long cb = dbits(c);
+    unsigned d;
+    const long long C = (long long)(((cb & kFrac52) | kHidden52) << 1);
+    return pack_units(lap_units(x, (unsigned)(cb >> 52), C, d) - C, c);
+}
+
+// L from integers; false when some operation of the FP64 order might round (then L is not set)
+__host__ __device__ __forceinline__ bool lap6_int(double c, double x0, double x1, double x2, double x3, double x4,
+                                                  double x5, double& L) {
+    const Lap6Sum k = lap6_exact_sum(c, x0, x1, x2, x3, x4, x5);
+    if (k.exact) L = pack_units(k.S, c);
+    return k.exact;
+}
+
+// the six differences from integers, in one pass; false (d not set) unless every difference is exact
 __host__ __device__ __forceinline__ bool lap6_diffs(double c, double x0, double x1, double x2, double x3, double x4,
                                                     double x5, double (&d)[6]) {
     const unsigned long long cb = dbits(c);
     const unsigned hc = (unsigned)(cb >> 52);
-    const unsigned ec = hc & 0x7ffu;
     const long long C = (long long)(((cb & kFrac52) | kHidden52) << 1);
-    bool ok = ec >= 64u && ec <= 2000u;
-    long long D[6];
     const double x[6] = {x0, x1, x2, x3, x4, x5};
+    bool ok = true;
+    long long D[6], S = 0;
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
-        const unsigned long long xb = dbits(x[i]);
-        const unsigned e = (unsigned)(xb >> 52) - hc + 1u;
-        const long long X = (long long)(((xb & kFrac52) | kHidden52) << (e & 3u));
+        unsigned e;
+        const long long X = lap_units(x[i], hc, C, e);
         ok = ok && e <= 2u && 2 * X >= C && X <= 2 * C;
         D[i] = X - C;
+        S += D[i];
     }
+    ok = ok && lap_c_ok(cb, S);
     if (ok) {
 #pragma unroll
-        for (int i = 0; i < 6; ++i) d[i] = pack_units(D[i], ec, cb);
+        for (int i = 0; i < 6; ++i) d[i] = pack_units(D[i], c);
     }
     return ok;
 }

@@ -127,7 +127,7 @@ __device__ __forceinline__ DC<C> ldd(const double* p, bool ro) {
 }
 
 // The FP64 sweep of tile (bx, by) and z chunk bz: a warp owns a row of 32 C cells (C per lane).
-template <int WY, int C>
+template <int WY, int C, bool UNIFORM>
 __device__ __forceinline__ void sweep_f64(const SweepArgs& A, int bx, int by, int bz) {
     constexpr int TW = 32 * C;
     const double* __restrict__ phi_c = (const double*)A.hi_c;
@@ -177,7 +177,7 @@ __device__ __forceinline__ void sweep_f64(const SweepArgs& A, int bx, int by, in
             for (int e = 0; e < C; ++e) {
                 double l = e == 0 ? xl : cc.v[e - 1];
                 double rr = e == C - 1 ? xr : cc.v[e + 1];
-                o.v[e] = f64_update(l, rr, ys.v[e], yn.v[e], cm.v[e], cp.v[e], cc.v[e], pv.v[e], r.v[e], nu2);
+                o.v[e] = f64_update<UNIFORM>(l, rr, ys.v[e], yn.v[e], cm.v[e], cp.v[e], cc.v[e], pv.v[e], r.v[e], nu2);
             }
             if (!idx_ok(q, C, L.elems, B.err)) {
             } else if (C == 4 && full) {
@@ -219,12 +219,13 @@ __device__ __forceinline__ void sweep_f64(const SweepArgs& A, int bx, int by, in
     }
 }
 
-template <int WY>
+// UNIFORM: the FP64 forms chosen per warp (batched launches) or per lane (the single-grid sweep), cell.cuh
+template <int WY, bool UNIFORM>
 __device__ __forceinline__ void sweep_f64_any(const SweepArgs& A, int bx, int by, int bz) {
     if (A.cpl == 1)
-        sweep_f64<WY, 1>(A, bx, by, bz);
+        sweep_f64<WY, 1, UNIFORM>(A, bx, by, bz);
     else
-        sweep_f64<WY, 4>(A, bx, by, bz);
+        sweep_f64<WY, 4, UNIFORM>(A, bx, by, bz);
 }
 
 constexpr int kWY = 8;
@@ -315,7 +316,7 @@ int zchunk(const hg_grid* g) {
 
 template <int WY>
 __global__ void __launch_bounds__(32 * WY, 2) k_step_f64(const SweepArgs A) {
-    sweep_f64_any<WY>(A, blockIdx.x, blockIdx.y, blockIdx.z);
+    sweep_f64_any<WY, false>(A, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
 // entry of block b in a prefix table of n entries
@@ -352,7 +353,7 @@ __global__ void __launch_bounds__(32 * (WY + 1), 2) k_step_batch(const TmaEntry*
                 asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&E.m[m]) : "memory");
         tma_sweep<WY, S>(&E.m[0], &E.m[1], &E.m[2], &E.m[3], E.A, bx, by, bz, E.err, smem, bars);
     } else {
-        sweep_f64_any<WY>(E.A, bx, by, bz);
+        sweep_f64_any<WY, true>(E.A, bx, by, bz);
     }
 }
 
@@ -381,7 +382,7 @@ __global__ void __launch_bounds__(32 * WY, 2) k_batch_f64(const TmaEntry* __rest
     const int e = batch_entry(first, n, blockIdx.x);
     const SweepArgs& A = tab[e].A;
     const unsigned local = blockIdx.x - __ldg(first + e);
-    sweep_f64_any<WY>(A, (int)(local % A.gx), (int)((local / A.gx) % A.gy), (int)(local / (A.gx * A.gy)));
+    sweep_f64_any<WY, true>(A, (int)(local % A.gx), (int)((local / A.gx) % A.gy), (int)(local / (A.gx * A.gy)));
 }
 
 }  // namespace
