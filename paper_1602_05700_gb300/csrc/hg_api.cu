@@ -377,7 +377,7 @@ int hg_set_temporal_depth(hg_grid* g, int k) {
         return fail(HG_ERR_STATE, "a slab exchanges its interface planes before every sub-step: temporal depth 1 only");
     if (k > 1 && g->prec != HG_PREC_F32K)
         return fail(HG_ERR_ARG, "temporal blocking is built for HG_PREC_F32K only (FP64 sub-steps are bound by the "
-                                "FP64 pipe, not by HBM traffic, so fusing them saves nothing)");
+                                "FP64 and integer pipes, at 22-41%% of HBM bandwidth, so fusing them saves nothing)");
     if (k > 1 && !g->dlt[1]) {
         size_t bytes = (size_t)g->L.elems * g->esize;
         HG_CUDA(cudaMalloc(&g->dlt[1], bytes));
