@@ -1,5 +1,6 @@
-"""Parity at the benchmark's full size and launch configuration (512^3, Robin, the orbiting-blob density, the
-default z chunks the bench uses): sampled outputs against the oracle, plus a whole-grid property.
+"""Parity at the benchmark's full size and launch configurations (512^3, Robin, the orbiting-blob density, the
+default z chunks the bench uses, single sweeps and the depth-2 fused kernel the headline step runs): sampled outputs
+against the oracle, plus a whole-grid property.
 
 After n sub-steps a cell depends only on the initial state within n cells of it (the stencil reaches one cell per
 sub-step), so the oracle computes a sampled output on a (2n+1)^3 sub-grid around it, whose frozen ghost layer holds
@@ -38,8 +39,10 @@ def state():
     return W, rho, phi0, prev0, pts
 
 
-def run_gpu(W, rho, phi0, prev0, prec):
+def run_gpu(W, rho, phi0, prev0, prec, depth=1):
     g = hg.Grid(N, N, N, W["h"], W["origin"], W["c"], W["G"], W["dt"], prec, "robin")
+    if depth > 1:
+        g.set_temporal_depth(depth)  # the default (not exact) mode, as the bench runs it
     g.set_density(rho if prec == "f32k" else rho.double())
     g.set_phi(phi0, prev0)
     g.step(NSUB)
@@ -72,9 +75,10 @@ def test_fp64_full_size_bit_exact_on_samples(state):
     assert np.array_equal(g, want), f"max |diff| {np.abs(g - want).max():.3e}"
 
 
-def test_f32k_full_size_on_samples_and_against_fp64(state):
+@pytest.mark.parametrize("depth", [1, 2])
+def test_f32k_full_size_on_samples_and_against_fp64(state, depth):
     W, rho, phi0, prev0, pts = state
-    got = run_gpu(W, rho, phi0, prev0, "f32k")
+    got = run_gpu(W, rho, phi0, prev0, "f32k", depth)
     want = oracle_samples(W, rho.double().cpu().numpy(), phi0, prev0, pts)
     g = got[pts[:, 2], pts[:, 1], pts[:, 0]]
     l2 = np.linalg.norm(g - want) / np.linalg.norm(want)
