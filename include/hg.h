@@ -279,6 +279,10 @@ int hg_batch_info(const hg_batch* b, int* z_planes_per_block, long long* blocks_
  * first hg_batch_step and cached per device and set of grids for the life of the process (an autotuner of this
  * library; the paper has no counterpart). */
 int hg_batch_tuning(const hg_batch* b, int out[4]);
+/* Pin the launch mode instead of letting the autotuner choose it: mode 1 = split (one launch per precision class per
+ * sub-step, two streams), 0 = one launch for both, -1 = autotuned (the default).  The other knobs are still tuned, on
+ * the next hg_batch_step; results do not depend on any of them.  HG_ERR_ARG for another mode. */
+int hg_batch_set_split(hg_batch* b, int mode);
 void hg_batch_free(hg_batch* b);
 
 /*

@@ -371,6 +371,12 @@ class Batch:
     def step(self, n=1):
         _lib.check(_lib.lib().hg_batch_step(self._h, int(n)))
 
+    def set_split(self, mode):
+        """Pin the launch mode: True = one launch per precision class per sub-step, False = one launch for both,
+        None = autotuned (the default).  Results do not depend on it."""
+        m = -1 if mode is None else (1 if mode else 0)
+        _lib.check(_lib.lib().hg_batch_set_split(self._h, m))
+
     def info(self):
         zb, nb = ctypes.c_int(), ctypes.c_longlong()
         _lib.check(_lib.lib().hg_batch_info(self._h, ctypes.byref(zb), ctypes.byref(nb)))

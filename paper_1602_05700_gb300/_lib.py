@@ -85,6 +85,7 @@ SIGNATURES = {
     "hg_batch_step": (_I, [_V, _I]),
     "hg_batch_info": (_I, [_V, _P(_I), _P(ctypes.c_longlong)]),
     "hg_batch_tuning": (_I, [_V, _P(_I)]),
+    "hg_batch_set_split": (_I, [_V, _I]),
     "hg_batch_free": (None, [_V]),
     "hg_moments_noalloc": (_I, [_V, _I, _I, _I, _I, _D, _P(_D), _I, _V, _I, _V]),
     "hg_probe_rate": (_I, [_I, _P(_D), _P(_D)]),

@@ -48,6 +48,7 @@ struct hg_batch {
     int cpl;   // FP64 cells per lane: 0 = per grid, whichever tile row fits better; 4 = 128-cell rows everywhere
     int zb32;  // compensated-float (TMA-staged) planes per block
     int split; // 1: FP64 and compensated-float entries as two launches per sub-step, on two streams
+    int force_split;  // -1: the autotuner chooses split; 0 or 1: pinned by hg_batch_set_split
     // split mode: the two classes' own prefix tables (FP64 entries first in the table, then the float ones)
     cudaStream_t stream2;
     cudaEvent_t ev_fork, ev_join;
@@ -80,6 +81,7 @@ std::string tune_key(const hg_batch* b) {
     std::sort(parts.begin(), parts.end());
     std::string k = p.name;
     for (auto& s : parts) k += ";" + s;
+    k += ";split=" + std::to_string(b->force_split);
     return k;
 }
 
@@ -201,11 +203,12 @@ int autotune(hg_batch* b, int budget, int* taken) {
         any32 = any32 || g->prec == HG_PREC_F32K;
     }
     std::vector<Tuning> cand;
+    const int split0 = b->force_split > 0 ? 1 : 0;
     if (any64)
         for (int cpl : {0, 4})
-            for (int zb : {8, 16, 32, 64}) cand.push_back({zb, cpl, 8, 0});
+            for (int zb : {8, 16, 32, 64}) cand.push_back({zb, cpl, 8, split0});
     else
-        cand.push_back({8, 0, 8, 0});
+        cand.push_back({8, 0, 8, split0});
     Tuning best = cand[0];
     float best_ms = -1.f;
     cudaEvent_t e0, e1;
@@ -243,7 +246,7 @@ int autotune(hg_batch* b, int budget, int* taken) {
     };
     for (const Tuning& t : cand)
         if (!time_one(t)) break;
-    if (rc == HG_OK && complete && best_ms >= 0.f) {  // each precision class as a launch of its own
+    if (rc == HG_OK && complete && best_ms >= 0.f && b->force_split < 0) {  // each class as a launch of its own
         Tuning t = best;
         t.split = 1;
         time_one(t);
@@ -260,7 +263,7 @@ int autotune(hg_batch* b, int budget, int* taken) {
         b->zb = 8;
         b->cpl = 0;
         b->zb32 = 8;
-        b->split = 0;
+        b->split = split0;
         return upload_tables(b);
     }
     b->zb = best.zb;
@@ -315,6 +318,7 @@ int hg_batch_create(hg_grid* const* grids, int n, hg_batch** out) {
     if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
     hg_batch* b = new hg_batch();
     b->n = n;
+    b->force_split = -1;
     b->grids.assign(grids, grids + n);
     b->device = grids[0]->device;
     int rc = HG_OK;
@@ -379,6 +383,17 @@ int hg_batch_step(hg_batch* b, int n_substeps) {
     }
     HG_CUDA(cudaEventRecord(b->ev_out, b->stream));
     HG_CUDA(cudaStreamWaitEvent(gs, b->ev_out, 0));
+    return HG_OK;
+}
+
+int hg_batch_set_split(hg_batch* b, int mode) {
+    HG_RANGE("hg_batch_set_split");
+    if (!b) return fail(HG_ERR_ARG, "null batch");
+    if (mode < -1 || mode > 1) return fail(HG_ERR_ARG, "mode must be -1 (autotuned), 0 or 1");
+    if (mode == b->force_split) return HG_OK;
+    b->force_split = mode;
+    b->zb = 0;  // the next hg_batch_step tunes (or finds in the cache) the launch for this mode
+    destroy_graph(b);
     return HG_OK;
 }
 

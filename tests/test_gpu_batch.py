@@ -49,6 +49,32 @@ def test_batch_equals_individual_steps():
         assert ga.stats()["step"] == gb.stats()["step"]
 
 
+@pytest.mark.parametrize("subset", ["mixed", "f32k", "f64"])
+@pytest.mark.parametrize("split", [False, True])
+def test_pinned_launch_modes_equal_individual_steps(split, subset):
+    """Both launch modes, pinned (one launch for both precisions, or one per precision class on two streams), for a
+    mixed batch and for each class alone: bit-identical to stepping each grid alone, across a mode change."""
+    specs = [sp for sp in SPECS if subset == "mixed" or sp[1] == subset]
+    a = make(specs, 90)
+    b = make(specs, 90)
+    batch = hg.Batch(a)
+    batch.set_split(split)
+    batch.step(9)
+    assert batch.info()["precisions_in_separate_launches"] == split
+    batch.set_split(not split)  # re-tuned for the other mode on the next step
+    batch.step(5)
+    assert batch.info()["precisions_in_separate_launches"] == (not split)
+    batch.set_split(None)
+    batch.step(4)
+    for g in b:
+        g.step(18)
+    for ga, gb in zip(a, b):
+        assert np.array_equal(ga.phi_ghosted(), gb.phi_ghosted())
+    batch.free()
+    with pytest.raises(hg.HGError):
+        hg._lib.check(hg._lib.lib().hg_batch_set_split(None, 0))
+
+
 def test_batch_against_oracle():
     specs = [(24, "f64", "robin"), (20, "f32k", "robin"), (28, "f64", "multipole")]
     grids = make(specs, 80)
