@@ -3,7 +3,8 @@ exact-differences form or the plain FP64 form per cell, and every form must give
 built so that each form is taken, and the borders between them are crossed, inside one grid: smooth fields, steep
 Gaussian tails, sign changes, exact zeros next to subnormals and tiny normals, values at and one ulp around powers
 of two, and phi^{n-1} near and beyond 2 phi^n.  Robin boundary (its ghosts are FP64 operations of the written order
-on both sides), so the comparison is bit for bit, signs of zero included."""
+on both sides), so the comparison is bit for bit, signs of zero included.  The single-grid sweep chooses the form per
+lane, the batched launches per warp: both are run."""
 import numpy as np
 import pytest
 
@@ -88,3 +89,33 @@ def test_fp64_tiers_bit_exact(kind, with_source):
         same = G.view(np.uint64) == p.view(np.uint64)
         assert same.all(), f"{kind}: {int((~same).sum())} cells differ after {g.stats(check=False)['step']} sub-steps"
     g.free()
+
+
+@pytest.mark.parametrize("split", [False, True])
+def test_fp64_tiers_bit_exact_in_a_batch(split):
+    """The same fields as FP64 grids of one batch (forms chosen per warp), in both launch modes."""
+    nx, ny, nz = SHAPE
+    origin = (-0.5 * nx * H, -0.5 * ny * H, -0.5 * nz * H)
+    dt = robin_cfl(nx, ny, nz, H) * H / np.sqrt(3.0)
+    grids, refs = [], []
+    for i, kind in enumerate(SEEDS):
+        g = hg.Grid(nx, ny, nz, H, origin, 1.0, 1.0, dt, "f64", "robin")
+        og = O.Grid(nx, ny, nz, H, origin, 1.0, 1.0, dt, O.BC_ROBIN)
+        rho = I.noise(og.shape, 78 + i, 0.0, 2.0)
+        phi0, prev0 = fields(kind)
+        g.set_density(torch.from_numpy(rho).cuda())
+        g.set_phi(torch.from_numpy(phi0).cuda(), torch.from_numpy(prev0).cuda())
+        p, q = O.initial_state(og, rho, phi0=phi0, phi_prev0=prev0)
+        O.run(og, p, q, rho, 13)
+        grids.append(g)
+        refs.append(p)
+    b = hg.Batch(grids)
+    b.set_split(split)
+    b.step(13)  # autotunes on its first sub-steps, then replays the graph
+    for kind, g, p in zip(SEEDS, grids, refs):
+        G = g.phi_ghosted()
+        same = G.view(np.uint64) == p.view(np.uint64)
+        assert same.all(), f"{kind}: {int((~same).sum())} cells differ"
+    b.free()
+    for g in grids:
+        g.free()
